@@ -1,0 +1,220 @@
+"""Pins of the oracle's wall-normal reconstruction, donor selection and ghost
+value (Sect. 2.3, Eqs. local_wall_normal .. contact_angle_localization)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2607_25444_b300 import inputs as I
+
+
+def _geom(solid, periodic=(1, 1, 1), dim=3):
+    nz, ny, nx = solid.shape
+    o = O.Oracle(I.base_params(nx, ny, nz, dim=dim, periodic=periodic))
+    o.set_geometry(solid)
+    return o, o.wall_list()
+
+
+def _coords(idx, shape):
+    nz, ny, nx = shape
+    return idx % nx, (idx // nx) % ny, idx // (nx * ny)
+
+
+def test_flat_walls_axis_normals_and_donors():
+    solid = I.walls_z(6, 5, 7)
+    o, wl = _geom(solid, periodic=(1, 1, 0))
+    assert len(wl["idx"]) == 2 * 6 * 5
+    c, _ = O.lattice(3)
+    x, y, z = _coords(wl["idx"], solid.shape)
+    for k in range(len(x)):
+        nz = -1.0 if z[k] == 0 else 1.0   # points from the fluid into the wall
+        np.testing.assert_array_equal(wl["nw_f32"][k], [0, 0, nz])
+        np.testing.assert_array_equal(wl["nw"][k], [0, 0, nz])
+        # 9 fluid links: 1 axis (6) + 4 face diagonals (3) + 4 corners (2)
+        assert tuple(wl["ntilde6"][k]) == (0, 0, int(nz) * 26)
+        assert tuple(c[wl["qstar"][k]]) == (0, 0, -int(nz))
+    assert (np.diff(wl["idx"]) > 0).all()
+
+
+def test_single_fluid_cell_hand_case():
+    """A lone fluid node inside solid: every neighbour s has exactly one
+    fluid link c_q = x_f - x_s, so n~ = -w_q c_q, n_w = -c_q/|c_q| and the
+    donor is that link (Algorithm 1 by hand)."""
+    solid = np.ones((5, 5, 5), dtype=np.uint8)
+    solid[2, 2, 2] = 0
+    o, wl = _geom(solid)
+    assert len(wl["idx"]) == 26
+    c, _ = O.lattice(3)
+    x, y, z = _coords(wl["idx"], solid.shape)
+    for k in range(26):
+        cq = np.array([2 - x[k], 2 - y[k], 2 - z[k]])
+        m2 = int((cq * cq).sum())
+        assert tuple(wl["ntilde6"][k]) == tuple(-(6 // m2) * cq)
+        np.testing.assert_allclose(wl["nw"][k], -cq / math.sqrt(m2), atol=1e-15)
+        assert tuple(c[wl["qstar"][k]]) == tuple(cq)
+
+
+def test_staircase_45_degree_symmetry():
+    """Solid where x + z < k (periodic in y): mirror symmetry x <-> z forces
+    n_w parallel to (1, 0, 1) on the staircase faces, component by component
+    exactly."""
+    n = 12
+    z, y, x = np.meshgrid(np.arange(n), np.arange(4), np.arange(n), indexing="ij")
+    solid = ((x + z) < 10).astype(np.uint8)
+    solid[0] = 1
+    solid[-1] = 1
+    solid[:, :, 0] = 1
+    solid[:, :, -1] = 1
+    o, wl = _geom(solid, periodic=(0, 1, 0))
+    xs, ys, zs = _coords(wl["idx"], solid.shape)
+    diag = (xs + zs >= 7) & (xs + zs <= 9) & (xs >= 3) & (zs >= 3) & \
+        (xs <= n - 4) & (zs <= n - 4)
+    assert diag.sum() > 4
+    for k in np.nonzero(diag)[0]:
+        n6 = wl["ntilde6"][k]
+        assert n6[1] == 0 and n6[0] == n6[2] and n6[0] < 0
+        assert wl["nw_f32"][k][0] == wl["nw_f32"][k][2]
+
+
+def test_rotation_equivariance():
+    """Rotating the voxel geometry by 90 deg about z maps n~6 (integer) to the
+    rotated vector exactly."""
+    g = I.SplitMix64(5)
+    n = 8
+    solid = (I.fast_uniform((n, n, n), seed=99) < 0.35).astype(np.uint8)
+    o1, w1 = _geom(solid)
+    rot = np.ascontiguousarray(np.rot90(solid, k=1, axes=(1, 2)))  # (y,x) plane
+    o2, w2 = _geom(rot)
+    # map each rotated wall node back to the original coordinates
+    x1, y1, z1 = _coords(w1["idx"], solid.shape)
+    d1 = {(int(a), int(b), int(c)): w1["ntilde6"][k]
+          for k, (a, b, c) in enumerate(zip(x1, y1, z1))}
+    x2, y2, z2 = _coords(w2["idx"], rot.shape)
+    assert len(x2) == len(x1)
+    # np.rot90 with axes (1,2): rot[z, i, j] = solid[z, j, n-1-i]
+    for k in range(len(x2)):
+        xo, yo = n - 1 - y2[k], x2[k]
+        v = d1[(int(xo), int(yo), int(z2[k]))]
+        vr = w2["ntilde6"][k]
+        # original vector (vx, vy) seen in rotated frame: (vy, -vx)
+        assert (vr[0], vr[1], vr[2]) == (-v[1], v[0], v[2]) or \
+               (vr[0], vr[1], vr[2]) == (v[1], -v[0], v[2])
+    _ = g
+
+
+def test_donor_is_exact_argmax_and_positive():
+    """Brute force over random geometries: the donor is a fluid link whose
+    score (-c_q . n_w)/|c_q| is maximal (float scores, exact ties allowed)
+    and strictly positive; ties go to the lowest q."""
+    c, _ = O.lattice(3)
+    for seed in (1, 2, 3):
+        n = 7
+        solid = (I.fast_uniform((n, n, n), seed=seed) < 0.5).astype(np.uint8)
+        o, wl = _geom(solid)
+        xs, ys, zs = _coords(wl["idx"], solid.shape)
+        for k in range(len(xs)):
+            nw = wl["nw"][k]
+            best, scores = None, {}
+            for q in range(27):
+                if q == 13:
+                    continue
+                t = ((zs[k] + c[q, 2]) % n, (ys[k] + c[q, 1]) % n,
+                     (xs[k] + c[q, 0]) % n)
+                if solid[t]:
+                    continue
+                scores[q] = float(-(c[q] @ nw) / np.linalg.norm(c[q]))
+            smax = max(scores.values())
+            q_star = int(wl["qstar"][k])
+            assert q_star in scores
+            assert scores[q_star] > 0
+            assert scores[q_star] >= smax - 1e-12
+            ties = [q for q, s in scores.items() if s >= smax - 1e-12]
+            assert q_star == min(ties)
+            _ = best
+
+
+def test_sphere_normals_radial_on_axes():
+    """Solid ball: on the six symmetry axes the reconstructed normal is
+    exactly radial (pointing into the ball); two shells of wall nodes lie on
+    each axis (the inner one touches the fluid through corner links)."""
+    n = 21
+    ctr = (10, 10, 10)
+    solid = I.sphere_solid(n, n, n, ctr, 6.0)
+    o, wl = _geom(solid)
+    xs, ys, zs = _coords(wl["idx"], solid.shape)
+    hits = 0
+    for k in range(len(xs)):
+        d = np.array([xs[k] - 10, ys[k] - 10, zs[k] - 10])
+        if (d != 0).sum() == 1:
+            hits += 1
+            np.testing.assert_array_equal(wl["nw"][k], -np.sign(d))
+    assert hits == 12
+
+
+def test_non_periodic_axis_must_be_closed():
+    solid = np.zeros((5, 4, 4), dtype=np.uint8)
+    solid[0] = 1  # top layer missing
+    o = O.Oracle(I.base_params(4, 4, 5, periodic=(1, 1, 0)))
+    with pytest.raises(RuntimeError):
+        o.set_geometry(solid)
+
+
+def test_ghost_closed_forms_flat_wall():
+    """Flat wall below the fluid: n_w = r_fs = (0,0,-1) gives
+    g = phi_f + lambda_s |grad_par phi_f| cot(theta); theta = 90 deg is the
+    neutral mirror; phi_f in {0, 1} gives g = phi_f; the normal gradient
+    component does not enter."""
+    nw = np.array([0.0, 0.0, -1.0])
+    rfs = np.array([0.0, 0.0, -1.0])
+    g = I.SplitMix64(3)
+    for _ in range(20):
+        phi_f = g.uniform(0.05, 0.95)
+        grad = np.array([g.uniform(-0.3, 0.3) for _ in range(3)])
+        th = g.uniform(20.0, 160.0)
+        lam = math.sqrt(4 * phi_f * (1 - phi_f))
+        tpar = math.hypot(grad[0], grad[1])
+        exp = phi_f + lam * tpar / math.tan(math.radians(th))
+        got = O.ghost_value(phi_f, grad, nw, rfs, th)
+        assert abs(got - exp) < 1e-13
+        grad2 = grad.copy()
+        grad2[2] += 0.7
+        assert abs(O.ghost_value(phi_f, grad2, nw, rfs, th) - got) < 1e-13
+        assert abs(O.ghost_value(phi_f, grad, nw, rfs, 90.0) - phi_f) < 1e-15
+        if th < 89.0 and tpar > 1e-3:
+            assert got > phi_f
+        if th > 91.0 and tpar > 1e-3:
+            assert got < phi_f
+    for pf in (0.0, 1.0):
+        assert O.ghost_value(pf, [0.3, 0.1, 0.2], nw, rfs, 40.0) == pf
+
+
+def test_ghost_cot_regularisation():
+    """|sin theta_c| below tolerance: cot replaced by +-1e6 (Sect. 2.3)."""
+    nw = np.array([0.0, 0.0, -1.0])
+    rfs = np.array([0.0, 0.0, -1.0])
+    grad = np.array([0.1, 0.0, 0.0])
+    v180 = O.ghost_value(0.5, grad, nw, rfs, 180.0)  # theta_c = 0, cot -> +1e6
+    assert abs(v180 - (0.5 - 0.1 * 1e6)) < 1e-6
+    v0 = O.ghost_value(0.5, grad, nw, rfs, 0.0)  # theta_c = pi, cot -> -1e6
+    assert abs(v0 - (0.5 + 0.1 * 1e6)) < 1e-6
+
+
+def test_ghost_update_is_jacobi():
+    """All ghosts are computed from the field as it was before the pass:
+    running the pass twice on a field whose donors see no wall node gives the
+    same ghosts (the first pass's writes do not feed each other)."""
+    n = 10
+    solid = I.walls_z(n, n, n)
+    phi = I.droplet(n, n, n, (5, 5, 0.5), 4.0, 4.0).astype(np.float64)
+    o = O.Oracle(I.base_params(n, n, n, theta_deg=50.0))
+    o.set_geometry(solid)
+    o.set_fields(phi)
+    o.ghost_update()
+    a = o.fields()[0].copy()
+    o.ghost_update()
+    b = o.fields()[0]
+    # donors sit on z = 1 and z = n-2; their stencils include ghost nodes, so
+    # the second pass may differ, but only through those ghost reads
+    assert np.array_equal(a[1:-1], b[1:-1])
+    assert np.isfinite(b).all()
