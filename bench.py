@@ -1,0 +1,334 @@
+"""Throughput of the CAC-LB wetting step on B300: MLUPS and fraction of the
+HBM roofline.
+
+Workload (one GPU): the static-droplet case of the paper's Sect. 3.1 at
+256^3 -- walls at z = 0 and z = 255, periodic in x and y, a cap of radius 40
+centred on the bottom wall, theta = 60 deg, equal densities and viscosities
+(nu = 0.04), sigma = 0.02, W = 4, D = 0.02; synthetic seeded input. A step
+is one full pass of the method: ghost update, collide-stream, phi update,
+volume correction.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line. With N > 1 (torchrun) each rank runs an independent
+replica of the workload on its own GPU (the step needs no exchange between
+replicas); value is the total over ranks, timed by the slowest rank.
+--impl reference times the FP64 CPU oracle on this host's cores instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+GRID = 256
+THETA = 60.0
+METRIC = "MLUPS (CAC-LB step, 256^3)"
+# Algorithmic bytes of the collide-stream per fluid node: 27 populations
+# read + written (FP32), phi read, u written (3 x FP32), flags read.
+LB_BYTES_FLUID = 27 * 4 * 2 + 4 + 12 + 1
+LB_BYTES_SOLID = 1
+# Algorithmic bytes of one whole step per node: collide-stream 233, phi
+# update (phi read, u read, phi* written, flags) 21, correction 9.
+STEP_BYTES = LB_BYTES_FLUID + (4 + 12 + 4 + 1) + (4 + 4 + 1)
+L2_BYTES = 126 * 1024 * 1024
+
+
+def workload(grid=GRID, theta=THETA):
+    from paper_2607_25444_b300 import inputs as I
+    n = grid
+    p = I.base_params(n, n, n, sigma=0.02, theta_deg=theta)
+    solid = I.walls_z(n, n, n)
+    phi = I.droplet(n, n, n, (n / 2, n / 2, 0.5), 40.0 * grid / 256, p["width"])
+    return p, solid, phi
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_run(steps, max_seconds=30.0):
+    """FP64 oracle on the host cores, on the lower 64 layers of the same
+    workload (the cap is 40 high). Returns MLUPS, cores and the sample."""
+    from oracle import oracle as O
+    from paper_2607_25444_b300 import inputs as I
+    n, nz = GRID, 64
+    p = I.base_params(n, n, nz, sigma=0.02, theta_deg=THETA)
+    solid = I.walls_z(n, n, nz)
+    phi = I.droplet(n, n, nz, (n / 2, n / 2, 0.5), 40.0, p["width"])
+    o = O.Oracle(p)
+    o.set_geometry(solid)
+    o.set_fields(phi.astype(np.float64))
+    done, t0 = 0, time.perf_counter()
+    while done < steps:
+        o.step(1)
+        done += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    threads = int(os.environ.get("OMP_NUM_THREADS", cores))
+    return (n * n * nz * done / dt / 1e6, threads,
+            f"{done} step(s) of the 256x256x64 lower slab of the 256^3 "
+            f"static-droplet workload (walls z=0 and z=63), FP64, "
+            f"{dt:.1f} s")
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    steps = max(1, args.steps // 100)
+    total = 0.0
+    vals = []
+    for _ in range(max(1, min(args.warmup, 1))):
+        cpu_oracle_run(1, max_seconds=60.0)
+    for _ in range(1):
+        v, cores, sample = cpu_oracle_run(steps, max_seconds=60.0)
+        vals.append(v)
+        total += v
+    v = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "static droplet 256^3 (lower 64-layer slab on "
+                               "the CPU)", "grid": [GRID, GRID, GRID]},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def time_lb_kernel(solver, torch, reps):
+    """Average duration of one collide-stream launch (CUDA events on the
+    library's stream, which is torch's current stream)."""
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    torch.cuda.synchronize()
+    for i in range(reps):
+        starts[i].record(stream)
+        solver.lb_collide()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([s.elapsed_time(e) for s, e in zip(starts, ends)])) / 1e3
+
+
+def run_cuda(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2607_25444_b300 import cacl
+
+    # a dedicated stream: the library and the CUDA events share it
+    torch.cuda.set_stream(torch.cuda.Stream())
+    p, solid, phi = workload()
+    N = phi.size
+    fluid = int((solid == 0).sum())
+    s = cacl.Solver(p)
+    s.set_geometry(solid)
+    s.set_fields(phi)
+    W = s.info()["wall_count"]
+    kernels_per_step = 4 + (2 if W > 0 else 0)
+
+    # warm-up, then K timed steps bracketed by barrier + synchronize
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        s.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    dt = ev0.elapsed_time(ev1) / 1e3
+    s.check_finite()
+    mass = s.mass()
+    phi_now = s.fields()[0]
+    m_now = float(phi_now.astype(np.float64)[solid == 0].sum())
+    drift = abs(m_now - mass["m_ref"]) / mass["m_ref"]
+
+    t = torch.tensor([dt], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    dt_max = float(t.item())
+    value = world * N * args.steps / dt_max / 1e6
+
+    # dominant kernel: the collide-stream, timed alone
+    reps = max(5, min(50, args.steps))
+    lb_s = time_lb_kernel(s, torch, reps)
+    lb_bytes = fluid * LB_BYTES_FLUID + (N - fluid) * LB_BYTES_SOLID
+    peak, peak_kind = measured_peaks()
+    achieved = lb_bytes / lb_s / 1e9
+    step_gbs = N * STEP_BYTES * args.steps / dt / 1e9
+
+    # end to end through the C ABI with pinned host buffers
+    ph_host = torch.empty(N, dtype=torch.float32, pin_memory=True).numpy()
+    u_host = torch.zeros(3 * N, dtype=torch.float32, pin_memory=True).numpy()
+    out_phi = torch.empty(N, dtype=torch.float32, pin_memory=True).numpy()
+    out_u = torch.empty(3 * N, dtype=torch.float32, pin_memory=True).numpy()
+    ph_host[:] = phi.reshape(-1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_fields(ph_host, u_host)
+    s.step(args.steps)
+    s.L.cacl_get_fields(s.h, cacl._ptr(out_phi), cacl._ptr(out_u), None, 0)
+    torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - t0
+    e2e = N * args.steps / e2e_dt / 1e6 * world
+    h2d = (ph_host.nbytes + u_host.nbytes) / args.steps
+    d2h = (out_phi.nbytes + out_u.nbytes) / args.steps
+    s.close()
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        v, cores, sample = cpu_oracle_run(2, max_seconds=30.0)
+        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": sample}
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt_max / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "static droplet on a flat wall, 256^3, R0=40, "
+                               "theta=60 deg, equal densities, nu=0.04, "
+                               "sigma=0.02, W=4, D=0.02",
+                   "grid": [GRID, GRID, GRID], "storage": "f32",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (populations 2 x 1.8 GB)",
+                   "wall_nodes": W, "fluid_nodes": fluid},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "lb_collide_f32",
+                     "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": lb_bytes,
+                     "launch_ms": lb_s * 1e3},
+        "step_roofline": {"bytes_per_node": STEP_BYTES, "achieved": step_gbs,
+                          "frac": step_gbs / peak,
+                          "ideal_mlups": peak * 1e9 / STEP_BYTES / 1e6},
+        "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": kernels_per_step * args.steps,
+        "clocks": clk.summary(),
+        "checks": {"mass_drift_rel": drift, "lambda": mass["lam"]},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip the CPU-oracle baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cuda(args)
+
+
+if __name__ == "__main__":
+    main()

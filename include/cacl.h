@@ -1,0 +1,178 @@
+/*
+ * cacl.h -- C ABI of the B300 (sm_103a) CAC-LB wetting step.
+ *
+ * One time step of the conservative Allen-Cahn lattice Boltzmann scheme with
+ * the geometric wetting boundary condition of arXiv 2607.25444:
+ *   1. ghost phi values at wall nodes from the reconstructed wall normal and
+ *      a donor fluid node at the imposed contact angle (Sect. 2.3,
+ *      Eqs. local_wall_normal .. contact_angle_localization, Algorithm 1);
+ *   2. the D3Q27 pull collide-stream: third-order Hermite equilibrium,
+ *      recursive regularisation, Guo forcing with the chemical-potential
+ *      capillary force, the pressure and viscous corrections and gravity
+ *      (Sect. 2.1, Eqs. lbe .. lap_iso);
+ *   3. the conservative Allen-Cahn update with MUSCL-minmod advection,
+ *      isotropic diffusion and the isotropic compressive divergence
+ *      (Sect. 2.2, Eq. phi_update_muscl);
+ *   4. the global volume correction over the interface band (Sect. 2.4,
+ *      Eqs. tentative_phase_field_mass .. mass_corrected_phi).
+ *
+ * Conventions for every call:
+ *   - Grid: nx * ny * nz nodes, node n = x + nx*(y + ny*z), x fastest.
+ *   - Host pointers are read or written during the call only, never kept.
+ *   - All device work is enqueued on the stream given to cacl_create (NULL =
+ *     the legacy default stream). Calls that return data to host memory
+ *     synchronise that stream before returning.
+ *   - Every call returns a cacl_status. On error the context records a
+ *     message, readable with cacl_last_error; the state is unchanged unless
+ *     the message says otherwise.
+ *   - Required order: cacl_create -> cacl_set_geometry ->
+ *     [cacl_set_contact_angle] -> cacl_set_fields -> cacl_step ...
+ *     A call out of order returns CACL_ERR_STATE.
+ *   - The context owns all device memory it allocates; cacl_destroy frees it.
+ *   - Errors of the CUDA runtime are returned as CACL_ERR_CUDA.
+ */
+#ifndef CACL_H
+#define CACL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cacl_ctx cacl_ctx;
+
+typedef enum {
+  CACL_OK = 0,
+  CACL_ERR_ARG = -1,       /* invalid argument or size */
+  CACL_ERR_CUDA = -2,      /* CUDA runtime error */
+  CACL_ERR_STATE = -3,     /* call out of the required order */
+  CACL_ERR_GEOMETRY = -4,  /* non-periodic axis not closed by solid layers */
+  CACL_ERR_DIVERGED = -5,  /* non-finite phi or u found by cacl_check_finite */
+  CACL_ERR_TIMEOUT = -6    /* reserved for bounded device waits */
+} cacl_status;
+
+/* Storage of the populations; arithmetic is FP32 in every mode. */
+typedef enum {
+  CACL_F32 = 0,
+  CACL_F16_SHIFTED = 1,
+  CACL_BF16_SHIFTED = 2
+} cacl_storage;
+
+/*
+ * Problem statement (Sect. 2.1-2.4). All quantities in lattice units.
+ *   width      interface thickness delta (Eq. kappa_delta); > 0
+ *   mobility   interface diffusivity D; >= 0. kappa = 4 D / delta.
+ *   sigma      surface tension; beta = 12 sigma/delta, kappa_phi = 3 sigma
+ *              delta / 2 (Eq. Fcap)
+ *   rho_l/g    densities of liquid (phi = 1) and gas (phi = 0)
+ *   nu_l/g     kinematic viscosities; mu = rho nu mixes linearly
+ *              (Eq. mu_mix_linear)
+ *   gravity    g; the body force is F_ext = (rho(phi) - rho_g) g
+ *   theta_deg  contact angle of every wall node until set_contact_angle
+ *   eps_phi    band threshold of the volume correction weight chi
+ *              (Eq. interface_weight_mass_correction), 0 < eps_phi < 1/2
+ *   periodic   1 = periodic axis; 0 = axis closed by solid layers at 0 and
+ *              n-1 (checked by cacl_set_geometry)
+ */
+typedef struct {
+  int nx, ny, nz;
+  int periodic[3];
+  double width;
+  double mobility;
+  double sigma;
+  double rho_l, rho_g;
+  double nu_l, nu_g;
+  double gravity[3];
+  double theta_deg;
+  double eps_phi;
+  int storage; /* cacl_storage */
+} cacl_params;
+
+/* Validates *params and allocates the device state (populations x2, phi x2,
+ * velocity, flags, reduction scratch) on the current CUDA device.
+ * stream: a cudaStream_t or NULL. On success *out owns the state. */
+cacl_status cacl_create(const cacl_params* params, void* stream,
+                        cacl_ctx** out);
+
+/* Frees everything the context owns. NULL is accepted. */
+void cacl_destroy(cacl_ctx* ctx);
+
+/* Text of the last error recorded on ctx ("" if none). */
+const char* cacl_last_error(const cacl_ctx* ctx);
+
+/* Occupancy (host, N bytes, 1 = solid) -> flags, wall list (Sect. 2.3,
+ * Eqs. local_wall_normal .. donor_to_solid). For every solid node with fluid
+ * neighbours: integer normal n~6 = sum over fluid links of 6 w_q (-c_q)
+ * (w_q = 1, 1/2, 1/3), unit normal n_w = n~6/|n~6| rounded to FP32, donor
+ * q* = argmax (-c_q . n_w)/|c_q| compared exactly (ties: lowest q with
+ * q = 9(cz+1) + 3(cy+1) + (cx+1)). Nodes with n~6 = 0 are skipped. The wall
+ * list is sorted by node index. Contact angles reset to params.theta_deg;
+ * fields must be set again afterwards. Returns CACL_ERR_GEOMETRY when a
+ * non-periodic axis is not closed by solid layers. Synchronises. */
+cacl_status cacl_set_geometry(cacl_ctx* ctx, const uint8_t* solid);
+
+/* Contact angle per node in degrees (host, N floats, read at wall nodes
+ * only), or NULL for params.theta_deg everywhere (Eq.
+ * internal_contact_angle: theta_c = pi - theta; cot theta_c replaced by
+ * sign(cos theta_c) 1e6 when |sin theta_c| < 1e-6). */
+cacl_status cacl_set_contact_angle(cacl_ctx* ctx, const float* theta_deg);
+
+/* Initial state from host arrays: phi (N floats, every node; values at
+ * solid nodes seed the ghosts) and u (3N floats, component-major, or NULL
+ * for rest). Populations become f^eq(p* = 0, u) (Eq. feq3); the mass
+ * reference M_ref becomes the FP64 sum of phi over fluid nodes
+ * (Eq. phase_field_mass). */
+cacl_status cacl_set_fields(cacl_ctx* ctx, const float* phi, const float* u);
+
+/* Replace parts of the state (host arrays), e.g. to resume from a
+ * checkpoint: populations f* (27N floats, f[q*N + n]), phi (N), u (3N). */
+cacl_status cacl_set_populations(cacl_ctx* ctx, const float* f);
+cacl_status cacl_set_phi(cacl_ctx* ctx, const float* phi);
+cacl_status cacl_set_velocity(cacl_ctx* ctx, const float* u);
+cacl_status cacl_set_mass_ref(cacl_ctx* ctx, double m_ref);
+
+/* Advance nsteps >= 0 full steps (ghost update, collide-stream, phi update,
+ * volume correction) on the context stream; does not synchronise. */
+cacl_status cacl_step(cacl_ctx* ctx, int nsteps);
+
+/* The four parts of one step, enqueued singly (for inspection and part by
+ * part checks). cacl_lb_collide reads phi and writes populations and u;
+ * cacl_phase_update writes phi* and the block partial sums; cacl_volume_
+ * correct forms lambda and phi^{n+1} = phi* + lambda chi(phi*). */
+cacl_status cacl_ghost_update(cacl_ctx* ctx);
+cacl_status cacl_lb_collide(cacl_ctx* ctx);
+cacl_status cacl_phase_update(cacl_ctx* ctx);
+cacl_status cacl_volume_correct(cacl_ctx* ctx);
+
+/* Copy out phi (N), u (3N), p* (N, sum of f* at fluid nodes, 0 at solids);
+ * any pointer may be NULL. device_ptrs = 1: the pointers are device memory
+ * (copied on the context stream, no synchronisation); 0: host memory
+ * (synchronises). */
+cacl_status cacl_get_fields(cacl_ctx* ctx, float* phi, float* u, float* pstar,
+                            int device_ptrs);
+cacl_status cacl_get_populations(cacl_ctx* ctx, float* f, int device_ptrs);
+
+/* Wall list (host arrays sized by *count, which is always written):
+ * idx (node), qstar (donor direction), ntilde6 (3 per node), nw (FP32 unit
+ * normal, 3 per node). Pass NULL arrays to query the count. */
+cacl_status cacl_get_wall_list(cacl_ctx* ctx, int32_t* idx, int8_t* qstar,
+                               int16_t* ntilde6, float* nw, int32_t* count);
+
+/* FP64 mass bookkeeping of the last correction: M_ref, M* (sum phi* over
+ * fluid), W (sum chi), lambda. Synchronises. */
+cacl_status cacl_get_mass(cacl_ctx* ctx, double* m_ref, double* m_star,
+                          double* w_sum, double* lambda);
+
+/* Returns CACL_ERR_DIVERGED if phi or u holds a NaN or Inf. Synchronises. */
+cacl_status cacl_check_finite(cacl_ctx* ctx);
+
+/* Grid size N and bytes of device memory the context holds. */
+cacl_status cacl_get_info(const cacl_ctx* ctx, int64_t* nodes,
+                          int64_t* device_bytes, int32_t* wall_count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CACL_H */

@@ -1,0 +1,264 @@
+"""Python binding of libcacl.so (include/cacl.h): argument marshalling only.
+
+Every step of the method runs in the library's sm_103a kernels. PyTorch
+supplies the CUDA stream (``torch.cuda.current_stream()``) and, for the
+device-pointer getters, device memory. There is no CPU fallback: if the
+library is missing or no GPU is present the calls raise.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcacl.so")
+
+CACL_OK = 0
+STATUS = {0: "CACL_OK", -1: "CACL_ERR_ARG", -2: "CACL_ERR_CUDA",
+          -3: "CACL_ERR_STATE", -4: "CACL_ERR_GEOMETRY",
+          -5: "CACL_ERR_DIVERGED", -6: "CACL_ERR_TIMEOUT"}
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+
+EXPORTS = (
+    "cacl_create", "cacl_destroy", "cacl_last_error", "cacl_set_geometry",
+    "cacl_set_contact_angle", "cacl_set_fields", "cacl_set_populations",
+    "cacl_set_phi", "cacl_set_velocity", "cacl_set_mass_ref", "cacl_step",
+    "cacl_ghost_update", "cacl_lb_collide", "cacl_phase_update",
+    "cacl_volume_correct", "cacl_get_fields", "cacl_get_populations",
+    "cacl_get_wall_list", "cacl_get_mass", "cacl_check_finite",
+    "cacl_get_info",
+)
+
+
+class CaclError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CaclParams(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("periodic", C.c_int * 3),
+        ("width", C.c_double), ("mobility", C.c_double), ("sigma", C.c_double),
+        ("rho_l", C.c_double), ("rho_g", C.c_double),
+        ("nu_l", C.c_double), ("nu_g", C.c_double),
+        ("gravity", C.c_double * 3),
+        ("theta_deg", C.c_double), ("eps_phi", C.c_double),
+        ("storage", C.c_int),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load libcacl.so; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"CUDA library not built: {LIB_PATH} is missing "
+            "(run __graft_entry__.build() or paper_2607_25444_b300/build.py)")
+    L = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    L.cacl_create.argtypes = [C.POINTER(CaclParams), vp, C.POINTER(vp)]
+    L.cacl_destroy.argtypes = [vp]
+    L.cacl_destroy.restype = None
+    L.cacl_last_error.argtypes = [vp]
+    L.cacl_last_error.restype = C.c_char_p
+    L.cacl_set_geometry.argtypes = [vp, vp]
+    L.cacl_set_contact_angle.argtypes = [vp, vp]
+    L.cacl_set_fields.argtypes = [vp, vp, vp]
+    L.cacl_set_populations.argtypes = [vp, vp]
+    L.cacl_set_phi.argtypes = [vp, vp]
+    L.cacl_set_velocity.argtypes = [vp, vp]
+    L.cacl_set_mass_ref.argtypes = [vp, C.c_double]
+    L.cacl_step.argtypes = [vp, C.c_int]
+    for name in ("cacl_ghost_update", "cacl_lb_collide", "cacl_phase_update",
+                 "cacl_volume_correct", "cacl_check_finite"):
+        getattr(L, name).argtypes = [vp]
+    L.cacl_get_fields.argtypes = [vp, vp, vp, vp, C.c_int]
+    L.cacl_get_populations.argtypes = [vp, vp, C.c_int]
+    L.cacl_get_wall_list.argtypes = [vp, vp, vp, vp, vp, C.POINTER(C.c_int32)]
+    dp = C.POINTER(C.c_double)
+    L.cacl_get_mass.argtypes = [vp, dp, dp, dp, dp]
+    L.cacl_get_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                C.POINTER(C.c_int32)]
+    for name in EXPORTS:
+        f = getattr(L, name)
+        if name not in ("cacl_destroy", "cacl_last_error"):
+            f.restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f32(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float32).reshape(-1)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def make_params(d):
+    p = CaclParams()
+    p.nx, p.ny, p.nz = int(d["nx"]), int(d["ny"]), int(d["nz"])
+    for a, v in enumerate(d.get("periodic", (1, 1, 0))):
+        p.periodic[a] = int(v)
+    p.width = float(d.get("width", 4.0))
+    p.mobility = float(d.get("mobility", 0.02))
+    p.sigma = float(d.get("sigma", 0.01))
+    p.rho_l = float(d.get("rho_l", 1.0))
+    p.rho_g = float(d.get("rho_g", 1.0))
+    p.nu_l = float(d.get("nu_l", 0.04))
+    p.nu_g = float(d.get("nu_g", 0.04))
+    for a, v in enumerate(d.get("gravity", (0.0, 0.0, 0.0))):
+        p.gravity[a] = float(v)
+    p.theta_deg = float(d.get("theta_deg", 90.0))
+    p.eps_phi = float(d.get("eps_phi", 1e-3))
+    st = d.get("storage", "f32")
+    p.storage = STORAGE[st] if isinstance(st, str) else int(st)
+    return p
+
+
+def current_stream():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the CAC-LB library runs on the GPU only")
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Solver:
+    """One CAC-LB state on the current CUDA device and stream.
+
+    ``params`` is a dict with the fields of cacl_params (D3Q27 only: a
+    two-dimensional problem is a periodic slab one node thick).
+    """
+
+    def __init__(self, params, stream=None):
+        self.L = load()
+        if params.get("dim", 3) != 3 and params.get("nz", 1) != 1:
+            raise ValueError("dim 2 runs as a D3Q27 slab with nz = 1")
+        self.params = dict(params)
+        self.p = make_params(params)
+        self.shape = (self.p.nz, self.p.ny, self.p.nx)
+        self.N = self.p.nx * self.p.ny * self.p.nz
+        s = current_stream() if stream is None else stream
+        h = C.c_void_p()
+        rc = self.L.cacl_create(C.byref(self.p), C.c_void_p(s), C.byref(h))
+        if rc != CACL_OK:
+            raise CaclError(rc, "cacl_create rejected the parameters or failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.cacl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != CACL_OK:
+            msg = self.L.cacl_last_error(self.h)
+            raise CaclError(rc, msg.decode() if msg else "")
+
+    # -- set-up
+    def set_geometry(self, solid):
+        s = np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1)
+        if s.size != self.N:
+            raise ValueError("occupancy has the wrong size")
+        self._check(self.L.cacl_set_geometry(self.h, _ptr(s)))
+
+    def set_contact_angle(self, theta_deg=None):
+        t = None if theta_deg is None else _f32(theta_deg, self.N)
+        self._check(self.L.cacl_set_contact_angle(self.h, _ptr(t)))
+
+    def set_fields(self, phi, u=None):
+        ph = _f32(phi, self.N)
+        uu = None if u is None else _f32(u, 3 * self.N)
+        self._check(self.L.cacl_set_fields(self.h, _ptr(ph), _ptr(uu)))
+
+    def set_populations(self, f):
+        self._check(self.L.cacl_set_populations(self.h, _ptr(_f32(f, 27 * self.N))))
+
+    def set_phi(self, phi):
+        self._check(self.L.cacl_set_phi(self.h, _ptr(_f32(phi, self.N))))
+
+    def set_velocity(self, u):
+        self._check(self.L.cacl_set_velocity(self.h, _ptr(_f32(u, 3 * self.N))))
+
+    def set_mass_ref(self, m):
+        self._check(self.L.cacl_set_mass_ref(self.h, float(m)))
+
+    # -- the step and its parts
+    def step(self, n=1):
+        self._check(self.L.cacl_step(self.h, int(n)))
+
+    def ghost_update(self):
+        self._check(self.L.cacl_ghost_update(self.h))
+
+    def lb_collide(self):
+        self._check(self.L.cacl_lb_collide(self.h))
+
+    def phase_update(self):
+        self._check(self.L.cacl_phase_update(self.h))
+
+    def volume_correct(self):
+        self._check(self.L.cacl_volume_correct(self.h))
+
+    # -- queries
+    def fields(self):
+        phi = np.empty(self.N, np.float32)
+        u = np.empty(3 * self.N, np.float32)
+        ps = np.empty(self.N, np.float32)
+        self._check(self.L.cacl_get_fields(self.h, _ptr(phi), _ptr(u), _ptr(ps), 0))
+        return (phi.reshape(self.shape), u.reshape((3,) + self.shape),
+                ps.reshape(self.shape))
+
+    def fields_device(self, phi=None, u=None, pstar=None):
+        """Copy into torch CUDA tensors (float32, contiguous) on the stream."""
+        def dp(t):
+            return None if t is None else C.c_void_p(t.data_ptr())
+        self._check(self.L.cacl_get_fields(self.h, dp(phi), dp(u), dp(pstar), 1))
+
+    def populations(self):
+        f = np.empty(27 * self.N, np.float32)
+        self._check(self.L.cacl_get_populations(self.h, _ptr(f), 0))
+        return f.reshape((27,) + self.shape)
+
+    def wall_list(self):
+        cnt = C.c_int32()
+        self._check(self.L.cacl_get_wall_list(self.h, None, None, None, None,
+                                              C.byref(cnt)))
+        W = cnt.value
+        idx = np.empty(W, np.int32)
+        q = np.empty(W, np.int8)
+        n6 = np.empty(3 * W, np.int16)
+        nw = np.empty(3 * W, np.float32)
+        self._check(self.L.cacl_get_wall_list(self.h, _ptr(idx), _ptr(q),
+                                              _ptr(n6), _ptr(nw), C.byref(cnt)))
+        return dict(idx=idx, qstar=q, ntilde6=n6.reshape(W, 3),
+                    nw_f32=nw.reshape(W, 3))
+
+    def mass(self):
+        v = [C.c_double() for _ in range(4)]
+        self._check(self.L.cacl_get_mass(self.h, *[C.byref(x) for x in v]))
+        return dict(m_ref=v[0].value, m_star=v[1].value, w_sum=v[2].value,
+                    lam=v[3].value)
+
+    def check_finite(self):
+        self._check(self.L.cacl_check_finite(self.h))
+
+    def info(self):
+        n, b, w = C.c_int64(), C.c_int64(), C.c_int32()
+        self._check(self.L.cacl_get_info(self.h, C.byref(n), C.byref(b), C.byref(w)))
+        return dict(nodes=n.value, device_bytes=b.value, wall_count=w.value)

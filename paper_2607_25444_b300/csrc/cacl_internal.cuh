@@ -1,0 +1,136 @@
+// cacl_internal.cuh -- shared device helpers and the context layout of the
+// sm_103a CAC-LB wetting step.
+//
+// Lattice: D3Q27, direction q = 9(cz+1) + 3(cy+1) + (cx+1), rest q = 13,
+// opposite direction 26 - q, weights 8/27, 2/27, 1/54, 1/216 by |c|^2
+// (Sect. 2.1), c_s^2 = 1/3. Everything is derived from q at compile time.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+
+#include "../../include/cacl.h"
+
+namespace cacl {
+
+constexpr int Q = 27;
+constexpr int REST = 13;
+
+__host__ __device__ constexpr int cx(int q) { return q % 3 - 1; }
+__host__ __device__ constexpr int cy(int q) { return (q / 3) % 3 - 1; }
+__host__ __device__ constexpr int cz(int q) { return q / 9 - 1; }
+__host__ __device__ constexpr int opp(int q) { return 26 - q; }
+__host__ __device__ constexpr int csq(int q) {
+  return cx(q) * cx(q) + cy(q) * cy(q) + cz(q) * cz(q);
+}
+__host__ __device__ constexpr float wq(int q) {
+  return csq(q) == 0 ? 8.0f / 27.0f
+       : csq(q) == 1 ? 2.0f / 27.0f
+       : csq(q) == 2 ? 1.0f / 54.0f
+                     : 1.0f / 216.0f;
+}
+
+// Node flags (one byte per node).
+constexpr uint8_t FLAG_SOLID = 1;  // node is solid
+constexpr uint8_t FLAG_NEAR = 2;   // fluid node with a solid neighbour
+constexpr uint8_t FLAG_WALL = 4;   // solid node that carries a ghost value
+
+struct Grid {
+  int nx, ny, nz;
+  int64_t N;
+};
+
+// Wrapped neighbour coordinate along one axis (every axis wraps; closed axes
+// have solid boundary layers, so a wrapped neighbour there is solid).
+__device__ __forceinline__ int wrap(int i, int d, int n) {
+  int j = i + d;
+  j = (j < 0) ? j + n : j;
+  return (j >= n) ? j - n : j;
+}
+
+// Scalar parameters uploaded once per context.
+struct Consts {
+  float rho_g, drho;      // rho = rho_g + drho * phi
+  float mu_g, dmu;        // mu = mu_g + dmu * phi
+  float beta4;            // 4 beta
+  float kappa_phi;        // kappa_phi
+  float gx, gy, gz;       // gravity
+  float mobility;         // D
+  float kappa;            // 4 D / delta
+  float eps_phi;
+};
+
+// Reduction partials of the phase update: per block (sum phi*, sum chi) as
+// doubles, plus the scalars formed from them.
+struct MassScalars {
+  double m_ref;
+  double m_star;
+  double w_sum;
+  double lambda;
+  float lambda_f;
+  int pad;
+};
+
+}  // namespace cacl
+
+struct cacl_ctx {
+  cacl_params p;
+  cacl::Grid g;
+  cacl::Consts k;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  bool has_geometry = false;
+  bool has_fields = false;
+
+  // device state
+  float* f[2] = {nullptr, nullptr};    // populations, [q][n], ping-pong
+  float* phi[2] = {nullptr, nullptr};  // phi^n (with ghosts) and phi*
+  float* u = nullptr;                  // [3][n]
+  uint8_t* flags = nullptr;
+  int fcur = 0;                         // buffer holding the current f*
+  int pcur = 0;                         // buffer holding the current phi
+
+  // wall list
+  int32_t wall_count = 0;
+  int32_t* w_idx = nullptr;
+  int32_t* w_donor = nullptr;
+  int8_t* w_q = nullptr;
+  int16_t* w_n6 = nullptr;  // [3][W]
+  float* w_nw = nullptr;    // [3][W]
+  float* w_cot = nullptr;   // cot(theta_c)
+  float* w_theta = nullptr; // theta in degrees
+  float* w_g = nullptr;     // ghost scratch
+
+  // reductions
+  int part_blocks = 0;
+  double* partials = nullptr;  // [2][part_blocks]
+  cacl::MassScalars* mass = nullptr;
+  int* scan_scratch = nullptr;
+  int scan_blocks = 0;
+
+  // one-step graphs, indexed by (fcur, pcur)
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  int* bad_flag = nullptr;  // device word for cacl_check_finite
+  int64_t device_bytes = 0;
+};
+
+// Kernel launchers (defined in the .cu files). All enqueue on c->stream.
+namespace cacl {
+cudaError_t launch_geometry(cacl_ctx* c, const uint8_t* solid_dev);
+cudaError_t launch_ghost(cacl_ctx* c, float* phi);
+cudaError_t launch_lb(cacl_ctx* c, const float* fin, float* fout,
+                      const float* phi);
+cudaError_t phase_init_attributes();
+cudaError_t launch_phase(cacl_ctx* c, const float* phi_in, float* phi_out);
+cudaError_t launch_correct(cacl_ctx* c, float* phi);
+cudaError_t launch_mass_ref(cacl_ctx* c, const float* phi);
+cudaError_t launch_init_populations(cacl_ctx* c);
+cudaError_t launch_pstar(cacl_ctx* c, const float* f, float* out);
+cudaError_t launch_check_finite(cacl_ctx* c, const float* phi, int* bad_dev);
+int phase_blocks(const cacl_ctx* c);
+int mass_ref_blocks(int64_t N);
+}  // namespace cacl

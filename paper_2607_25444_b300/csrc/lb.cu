@@ -1,0 +1,190 @@
+// lb.cu -- fused D3Q27 pull collide-stream with the multiphase forces
+// (Sect. 2.1: Eqs. pstar_moment, u_moment, rho_mix_linear, mu_mix_linear,
+// omega_phi, feq3, H2, H3, fneq3, A3rec, guo, Fsplit, Fcap, Fp, Fnu,
+// grad_iso, lap_iso).
+//
+// One thread per node, x fastest. Populations are structure-of-arrays
+// f[q][n]; the pull reads f*_q(x - c_q) (halfway bounce-back f*_{opp q}(x)
+// when x - c_q is solid), the phi stencil is read through the read-only
+// cache, and the node writes its 27 post-collision populations and u.
+//
+// Collision algebra. With A2 = Pi - p* c_s^2 I - u u + (u a + a u)/2 (the
+// second moment of f - (f^eq - S/2), using sum f^eq c c = p* c_s^2 I + u u),
+// tr = trace A2, v = A2 u, and for each direction cu = c.u, ca = c.a,
+// cAc = c.A2.c, cAu = c.v, the post-collision population
+//   f*_i = f^eq_i + (1 - omega) f^neq_i + S_i / 2
+// splits into a part even in c and a part odd in c:
+//   E = k1 + 4.5 cu^2 + om45 cAc + 4.5 cu ca
+//   O = cu (k2 + 4.5 cu^2 + 3 om45 cAc) - 2 om45 cAu + 1.5 ca
+//   f*(+c) = w (E + O),  f*(-c) = w (E - O)
+// with om45 = 4.5 (1 - omega), k1 = p* - 1.5 (u.u + u.a) - om45 tr / 3,
+// k2 = 3 - 4.5 u.u - om45 tr.
+#include "cacl_internal.cuh"
+
+namespace cacl {
+namespace {
+
+constexpr int LB_BX = 128;
+constexpr int LB_BY = 1;
+
+struct NodeOut {
+  float f[Q];
+  float ux, uy, uz;
+};
+
+__device__ __forceinline__ void collide(const float (&f)[Q], float phi0,
+                                        float gx, float gy, float gz, float lap,
+                                        const Consts& k, NodeOut& o) {
+  // moments over pairs of opposite directions (q < 13 has opposite 26 - q)
+  float p = f[REST], jx = 0.f, jy = 0.f, jz = 0.f;
+  float Pxx = 0.f, Pyy = 0.f, Pzz = 0.f, Pxy = 0.f, Pxz = 0.f, Pyz = 0.f;
+#pragma unroll
+  for (int q = 0; q < REST; ++q) {
+    const float s = f[q] + f[opp(q)];
+    const float d = f[q] - f[opp(q)];
+    p += s;
+    jx += cx(q) * d;
+    jy += cy(q) * d;
+    jz += cz(q) * d;
+    Pxx += (cx(q) * cx(q)) * s;
+    Pyy += (cy(q) * cy(q)) * s;
+    Pzz += (cz(q) * cz(q)) * s;
+    Pxy += (cx(q) * cy(q)) * s;
+    Pxz += (cx(q) * cz(q)) * s;
+    Pyz += (cy(q) * cz(q)) * s;
+  }
+  const float rho = k.rho_g + k.drho * phi0;
+  const float mu = k.mu_g + k.dmu * phi0;
+  const float inv_rho = 1.0f / rho;
+  const float nu = mu * inv_rho;
+  const float omega = 1.0f / (0.5f + 3.0f * nu);
+  const float grx = k.drho * gx, gry = k.drho * gy, grz = k.drho * gz;
+  const float muphi =
+      k.beta4 * phi0 * (phi0 - 1.0f) * (phi0 - 0.5f) - k.kappa_phi * lap;
+  const float p3 = p * (1.0f / 3.0f);
+  const float rb = rho - k.rho_g;
+  const float F0x = muphi * gx - p3 * grx + rb * k.gx;
+  const float F0y = muphi * gy - p3 * gry + rb * k.gy;
+  const float F0z = muphi * gz - p3 * grz + rb * k.gz;
+  // predictor for the viscous correction (Eq. Fnu)
+  const float a0x = F0x * inv_rho, a0y = F0y * inv_rho, a0z = F0z * inv_rho;
+  const float u0x = jx + 0.5f * a0x, u0y = jy + 0.5f * a0y, u0z = jz + 0.5f * a0z;
+  const float Q0xx = Pxx - p3 - u0x * u0x + u0x * a0x;
+  const float Q0yy = Pyy - p3 - u0y * u0y + u0y * a0y;
+  const float Q0zz = Pzz - p3 - u0z * u0z + u0z * a0z;
+  const float Q0xy = Pxy - u0x * u0y + 0.5f * (u0x * a0y + a0x * u0y);
+  const float Q0xz = Pxz - u0x * u0z + 0.5f * (u0x * a0z + a0x * u0z);
+  const float Q0yz = Pyz - u0y * u0z + 0.5f * (u0y * a0z + a0y * u0z);
+  const float cnu = -3.0f * nu * omega;
+  const float Fx = F0x + cnu * (Q0xx * grx + Q0xy * gry + Q0xz * grz);
+  const float Fy = F0y + cnu * (Q0xy * grx + Q0yy * gry + Q0yz * grz);
+  const float Fz = F0z + cnu * (Q0xz * grx + Q0yz * gry + Q0zz * grz);
+  const float ax = Fx * inv_rho, ay = Fy * inv_rho, az = Fz * inv_rho;
+  const float ux = jx + 0.5f * ax, uy = jy + 0.5f * ay, uz = jz + 0.5f * az;
+  const float Axx = Pxx - p3 - ux * ux + ux * ax;
+  const float Ayy = Pyy - p3 - uy * uy + uy * ay;
+  const float Azz = Pzz - p3 - uz * uz + uz * az;
+  const float Axy = Pxy - ux * uy + 0.5f * (ux * ay + ax * uy);
+  const float Axz = Pxz - ux * uz + 0.5f * (ux * az + ax * uz);
+  const float Ayz = Pyz - uy * uz + 0.5f * (uy * az + ay * uz);
+  const float tr = Axx + Ayy + Azz;
+  const float vx = Axx * ux + Axy * uy + Axz * uz;
+  const float vy = Axy * ux + Ayy * uy + Ayz * uz;
+  const float vz = Axz * ux + Ayz * uy + Azz * uz;
+  const float uu = ux * ux + uy * uy + uz * uz;
+  const float ua = ux * ax + uy * ay + uz * az;
+  const float om45 = 4.5f * (1.0f - omega);
+  const float k1 = p - 1.5f * (uu + ua) - om45 * tr * (1.0f / 3.0f);
+  const float k2 = 3.0f - 4.5f * uu - om45 * tr;
+  const float om3 = 3.0f * om45, om2 = 2.0f * om45;
+#pragma unroll
+  for (int q = 0; q < REST; ++q) {
+    const int X = cx(q), Y = cy(q), Z = cz(q);
+    const float cu = X * ux + Y * uy + Z * uz;
+    const float ca = X * ax + Y * ay + Z * az;
+    const float cAu = X * vx + Y * vy + Z * vz;
+    const float cAc = (X * X) * Axx + (Y * Y) * Ayy + (Z * Z) * Azz +
+                      2.0f * ((X * Y) * Axy + (X * Z) * Axz + (Y * Z) * Ayz);
+    const float cu2 = cu * cu;
+    const float E = k1 + 4.5f * cu2 + om45 * cAc + 4.5f * cu * ca;
+    const float O = cu * (k2 + 4.5f * cu2 + om3 * cAc) - om2 * cAu + 1.5f * ca;
+    o.f[q] = wq(q) * (E + O);
+    o.f[opp(q)] = wq(q) * (E - O);
+  }
+  o.f[REST] = wq(REST) * k1;
+  o.ux = ux;
+  o.uy = uy;
+  o.uz = uz;
+}
+
+__global__ void __launch_bounds__(LB_BX * LB_BY)
+lb_collide_f32(const float* __restrict__ fin, float* __restrict__ fout,
+               const float* __restrict__ phi, float* __restrict__ u,
+               const uint8_t* __restrict__ flags, Grid g, Consts k) {
+  const int x = blockIdx.x * LB_BX + threadIdx.x;
+  const int y = blockIdx.y * LB_BY + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return;
+  const int64_t nxy = (int64_t)g.nx * g.ny;
+  const int64_t n = x + (int64_t)g.nx * y + nxy * z;
+  const uint8_t fl = flags[n];
+  if (fl & FLAG_SOLID) return;
+  const int64_t N = g.N;
+  const int xo[3] = {wrap(x, -1, g.nx), x, wrap(x, 1, g.nx)};
+  const int yo[3] = {wrap(y, -1, g.ny) * g.nx, y * g.nx, wrap(y, 1, g.ny) * g.nx};
+  const int64_t zo[3] = {wrap(z, -1, g.nz) * nxy, z * nxy, wrap(z, 1, g.nz) * nxy};
+
+  float f[Q];
+  if (fl & FLAG_NEAR) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int64_t src = xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)];
+      const bool bb = (q != REST) && (__ldg(flags + src) & FLAG_SOLID);
+      f[q] = bb ? __ldg(fin + (int64_t)opp(q) * N + n)
+                : __ldg(fin + (int64_t)q * N + src);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int64_t src = xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)];
+      f[q] = __ldg(fin + (int64_t)q * N + src);
+    }
+  }
+
+  // isotropic gradient and Laplacian of phi (Eqs. grad_iso, lap_iso)
+  const float phi0 = __ldg(phi + n);
+  float gx = 0.f, gy = 0.f, gz = 0.f, ssum = 0.f;
+#pragma unroll
+  for (int q = 0; q < REST; ++q) {
+    const float vp = __ldg(phi + xo[1 + cx(q)] + yo[1 + cy(q)] + zo[1 + cz(q)]);
+    const float vm = __ldg(phi + xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)]);
+    const float dv = (3.0f * wq(q)) * (vp - vm);
+    gx += cx(q) * dv;
+    gy += cy(q) * dv;
+    gz += cz(q) * dv;
+    ssum += wq(q) * (vp + vm);
+  }
+  const float lap = 6.0f * (ssum - (1.0f - wq(REST)) * phi0);
+
+  NodeOut o;
+  collide(f, phi0, gx, gy, gz, lap, k, o);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) fout[(int64_t)q * N + n] = o.f[q];
+  u[n] = o.ux;
+  u[N + n] = o.uy;
+  u[2 * N + n] = o.uz;
+}
+
+}  // namespace
+
+cudaError_t launch_lb(cacl_ctx* c, const float* fin, float* fout,
+                      const float* phi) {
+  const Grid g = c->g;
+  dim3 block(LB_BX, LB_BY, 1);
+  dim3 grid((g.nx + LB_BX - 1) / LB_BX, (g.ny + LB_BY - 1) / LB_BY, g.nz);
+  lb_collide_f32<<<grid, block, 0, c->stream>>>(fin, fout, phi, c->u, c->flags,
+                                                g, c->k);
+  return cudaGetLastError();
+}
+
+}  // namespace cacl

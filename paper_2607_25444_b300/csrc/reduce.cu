@@ -1,0 +1,200 @@
+// reduce.cu -- volume correction (Sect. 2.4, Eqs. mass_defect,
+// interface_weight_mass_correction, mass_correction_normalization,
+// mass_corrected_phi), the initial state (Eq. feq3 at p* = 0), the mass
+// reference (Eq. phase_field_mass) and small state queries.
+//
+// The correction is deterministic: the phase update leaves one FP64 pair
+// (sum phi*, sum chi) per block; finalize_mass sums them in a fixed order in
+// one block and forms lambda = (M_ref - M*)/W (0 when W = 0);
+// correct_phi applies phi = phi* + lambda chi(phi*) at fluid nodes.
+#include "cacl_internal.cuh"
+
+namespace cacl {
+namespace {
+
+constexpr int FIN_THREADS = 1024;
+constexpr int ELEM_THREADS = 256;
+
+// Fixed-order sum of nb doubles at src (strided per thread, then a tree).
+__device__ double block_sum(const double* src, int nb, double* sh) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += FIN_THREADS) s += src[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = FIN_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(FIN_THREADS)
+finalize_mass(const double* __restrict__ partials, int nb, MassScalars* ms) {
+  __shared__ double sh[FIN_THREADS];
+  const double m = block_sum(partials, nb, sh);
+  const double w = block_sum(partials + nb, nb, sh);
+  if (threadIdx.x == 0) {
+    const double lam = (w > 0.0) ? (ms->m_ref - m) / w : 0.0;
+    ms->m_star = m;
+    ms->w_sum = w;
+    ms->lambda = lam;
+    ms->lambda_f = (float)lam;
+  }
+}
+
+__global__ void __launch_bounds__(FIN_THREADS)
+finalize_mass_ref(const double* __restrict__ partials, int nb,
+                  MassScalars* ms) {
+  __shared__ double sh[FIN_THREADS];
+  const double m = block_sum(partials, nb, sh);
+  if (threadIdx.x == 0) {
+    ms->m_ref = m;
+    ms->m_star = m;
+    ms->w_sum = 0.0;
+    ms->lambda = 0.0;
+    ms->lambda_f = 0.0f;
+  }
+}
+
+// phi = phi* + lambda chi(phi*) at fluid nodes, four nodes per thread.
+__global__ void __launch_bounds__(ELEM_THREADS)
+correct_phi(float* __restrict__ phi, const uint8_t* __restrict__ flags,
+            const MassScalars* __restrict__ ms, int64_t N, float eps) {
+  const float lam = ms->lambda_f;
+  const int64_t i4 = ((int64_t)blockIdx.x * ELEM_THREADS + threadIdx.x) * 4;
+  if (i4 + 3 < N) {
+    float4 v = *reinterpret_cast<const float4*>(phi + i4);
+    const uchar4 fl = *reinterpret_cast<const uchar4*>(flags + i4);
+    float* pv = &v.x;
+    const uint8_t fa[4] = {fl.x, fl.y, fl.z, fl.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float s = pv[j];
+      const float chi = (s > eps && s < 1.0f - eps) ? s * (1.0f - s) : 0.0f;
+      if (!(fa[j] & FLAG_SOLID)) pv[j] = fmaf(lam, chi, s);
+    }
+    *reinterpret_cast<float4*>(phi + i4) = v;
+  } else {
+    for (int64_t n = i4; n < N; ++n) {
+      const float s = phi[n];
+      const float chi = (s > eps && s < 1.0f - eps) ? s * (1.0f - s) : 0.0f;
+      if (!(flags[n] & FLAG_SOLID)) phi[n] = fmaf(lam, chi, s);
+    }
+  }
+}
+
+// FP64 block partials of sum phi over fluid nodes (once per set_fields).
+__global__ void __launch_bounds__(ELEM_THREADS)
+fluid_sum(const float* __restrict__ phi, const uint8_t* __restrict__ flags,
+          int64_t N, double* __restrict__ partials) {
+  __shared__ double sh[ELEM_THREADS];
+  double s = 0.0;
+  const int64_t base = (int64_t)blockIdx.x * ELEM_THREADS * 8;
+  for (int j = 0; j < 8; ++j) {
+    const int64_t n = base + j * ELEM_THREADS + threadIdx.x;
+    if (n < N && !(flags[n] & FLAG_SOLID)) s += (double)phi[n];
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = ELEM_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+// f = f^eq(p* = 0, u) (Eq. feq3) into both population buffers; u = 0 at
+// solid nodes.
+__global__ void __launch_bounds__(ELEM_THREADS)
+init_populations(float* __restrict__ f0, float* __restrict__ f1,
+                 float* __restrict__ u, const uint8_t* __restrict__ flags,
+                 int64_t N) {
+  const int64_t n = (int64_t)blockIdx.x * ELEM_THREADS + threadIdx.x;
+  if (n >= N) return;
+  float ux = u[n], uy = u[N + n], uz = u[2 * N + n];
+  if (flags[n] & FLAG_SOLID) {
+    ux = uy = uz = 0.f;
+    u[n] = 0.f;
+    u[N + n] = 0.f;
+    u[2 * N + n] = 0.f;
+  }
+  const float uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+    const float v = wq(q) * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu +
+                             4.5f * cu * (cu * cu - uu));
+    f0[(int64_t)q * N + n] = v;
+    f1[(int64_t)q * N + n] = v;
+  }
+}
+
+__global__ void __launch_bounds__(ELEM_THREADS)
+pstar_kernel(const float* __restrict__ f, const uint8_t* __restrict__ flags,
+             int64_t N, float* __restrict__ out) {
+  const int64_t n = (int64_t)blockIdx.x * ELEM_THREADS + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) s += f[(int64_t)q * N + n];
+  out[n] = (flags[n] & FLAG_SOLID) ? 0.f : s;
+}
+
+__global__ void __launch_bounds__(ELEM_THREADS)
+finite_kernel(const float* __restrict__ phi, const float* __restrict__ u,
+              const uint8_t* __restrict__ flags, int64_t N, int* bad) {
+  const int64_t n = (int64_t)blockIdx.x * ELEM_THREADS + threadIdx.x;
+  if (n >= N) return;
+  if (flags[n] & FLAG_SOLID) return;
+  const bool ok = isfinite(phi[n]) && isfinite(u[n]) && isfinite(u[N + n]) &&
+                  isfinite(u[2 * N + n]);
+  if (!ok) atomicOr(bad, 1);
+}
+
+int elem_blocks(int64_t N) { return (int)((N + ELEM_THREADS - 1) / ELEM_THREADS); }
+
+}  // namespace
+
+cudaError_t launch_correct(cacl_ctx* c, float* phi) {
+  finalize_mass<<<1, FIN_THREADS, 0, c->stream>>>(c->partials, c->part_blocks,
+                                                 c->mass);
+  const int64_t N = c->g.N;
+  const int nb = (int)((N + 4 * ELEM_THREADS - 1) / (4 * ELEM_THREADS));
+  correct_phi<<<nb, ELEM_THREADS, 0, c->stream>>>(phi, c->flags, c->mass, N,
+                                                 c->k.eps_phi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mass_ref(cacl_ctx* c, const float* phi) {
+  const int64_t N = c->g.N;
+  const int nb = (int)((N + ELEM_THREADS * 8 - 1) / (ELEM_THREADS * 8));
+  fluid_sum<<<nb, ELEM_THREADS, 0, c->stream>>>(phi, c->flags, N, c->partials);
+  finalize_mass_ref<<<1, FIN_THREADS, 0, c->stream>>>(c->partials, nb, c->mass);
+  return cudaGetLastError();
+}
+
+int mass_ref_blocks(int64_t N) {
+  return (int)((N + ELEM_THREADS * 8 - 1) / (ELEM_THREADS * 8));
+}
+
+cudaError_t launch_init_populations(cacl_ctx* c) {
+  init_populations<<<elem_blocks(c->g.N), ELEM_THREADS, 0, c->stream>>>(
+      c->f[0], c->f[1], c->u, c->flags, c->g.N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pstar(cacl_ctx* c, const float* f, float* out) {
+  pstar_kernel<<<elem_blocks(c->g.N), ELEM_THREADS, 0, c->stream>>>(
+      f, c->flags, c->g.N, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(cacl_ctx* c, const float* phi, int* bad_dev) {
+  finite_kernel<<<elem_blocks(c->g.N), ELEM_THREADS, 0, c->stream>>>(
+      phi, c->u, c->flags, c->g.N, bad_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace cacl

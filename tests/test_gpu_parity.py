@@ -1,0 +1,243 @@
+"""Parity of the sm_103a CUDA path (through the C ABI) with the FP64 CPU
+oracle on identical seeded inputs.
+
+Bars: bit-exact flags-derived wall lists (node, donor, integer normal, FP32
+unit normal); FP32 fields within max relative error 1e-5 of the oracle after
+one step (norm-wise per field: max |gpu - ref| / max |ref|) and within 1e-3
+in phi after 1000 steps.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2607_25444_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL_1STEP = 1e-5
+
+
+def _solver(params):
+    from paper_2607_25444_b300 import cacl
+    return cacl.Solver(params)
+
+
+def _pair(params, solid, phi, u=None, theta=None):
+    g = _solver(params)
+    g.set_geometry(solid)
+    if theta is not None:
+        g.set_contact_angle(theta)
+    g.set_fields(phi, u)
+    o = O.Oracle(params)
+    o.set_geometry(solid)
+    if theta is not None:
+        o.set_contact_angle(theta.astype(np.float64))
+    o.set_fields(phi.astype(np.float64),
+                 None if u is None else u.astype(np.float64))
+    return g, o
+
+
+def _rel(a, b):
+    den = np.abs(b).max()
+    return float(np.abs(a - b).max() / (den if den > 0 else 1.0))
+
+
+def _geometries():
+    yield "walls", I.walls_z(20, 18, 16), (1, 1, 0)
+    yield "orifice", I.orifice_plate(24, 24, 40, 16, 4, 8), (1, 1, 0)
+    n = 14
+    rnd = (I.fast_uniform((n, n, n), seed=21) < 0.4).astype(np.uint8)
+    yield "random", rnd, (1, 1, 1)
+    yield "sphere", I.sphere_solid(21, 21, 21, (10, 10, 10), 6.0), (1, 1, 1)
+    lone = np.ones((5, 5, 5), np.uint8)
+    lone[2, 2, 2] = 0
+    yield "lone", lone, (1, 1, 1)
+
+
+@pytest.mark.parametrize("name,solid,periodic",
+                         list(_geometries()), ids=lambda v: v if isinstance(v, str) else "")
+def test_wall_list_bit_exact(name, solid, periodic):
+    nz, ny, nx = solid.shape
+    p = I.base_params(nx, ny, nz, periodic=periodic)
+    g = _solver(p)
+    g.set_geometry(solid)
+    o = O.Oracle(p)
+    o.set_geometry(solid)
+    gw, ow = g.wall_list(), o.wall_list()
+    assert np.array_equal(gw["idx"], ow["idx"])
+    assert np.array_equal(gw["qstar"], ow["qstar"])
+    assert np.array_equal(gw["ntilde6"], ow["ntilde6"])
+    assert np.array_equal(gw["nw_f32"].view(np.uint32), ow["nw_f32"].view(np.uint32))
+
+
+def test_geometry_rejects_open_axis():
+    from paper_2607_25444_b300 import cacl
+    p = I.base_params(8, 8, 8, periodic=(1, 1, 0))
+    g = _solver(p)
+    with pytest.raises(cacl.CaclError):
+        g.set_geometry(np.zeros((8, 8, 8), np.uint8))
+
+
+def _droplet_case(nx=26, ny=22, nz=18, theta=60.0, **kw):
+    p = I.base_params(nx, ny, nz, sigma=0.01, rho_l=1.0, rho_g=0.1, nu_l=0.05,
+                      nu_g=0.1, theta_deg=theta, gravity=(0.0, 0.0, -2e-6), **kw)
+    solid = I.walls_z(nx, ny, nz)
+    phi = I.droplet(nx, ny, nz, (nx / 2, ny / 2, 0.5), 7.0, p["width"])
+    return p, solid, phi
+
+
+def test_ghost_update_part():
+    p, solid, phi = _droplet_case(theta=50.0)
+    g, o = _pair(p, solid, phi)
+    g.ghost_update()
+    o.ghost_update()
+    assert _rel(g.fields()[0], o.fields()[0]) < TOL_1STEP
+
+
+def test_lb_collide_part_random_populations():
+    p, solid, phi = _droplet_case()
+    g, o = _pair(p, solid, phi)
+    f = (I.random_state((p["nz"], p["ny"], p["nx"]), 27, seed=5, amp=2e-3))
+    g.set_populations(f)
+    o.set_populations(f.astype(np.float64))
+    g.lb_collide()
+    o.lb_collide()
+    gf, of = g.populations(), o.populations()
+    fluid = solid == 0
+    assert _rel(gf[:, fluid], of[:, fluid]) < TOL_1STEP
+    assert _rel(g.fields()[1], o.fields()[1]) < TOL_1STEP
+    assert _rel(g.fields()[2], o.fields()[2]) < TOL_1STEP
+
+
+def test_phase_update_part_random_velocity():
+    p, solid, phi = _droplet_case()
+    g, o = _pair(p, solid, phi)
+    u = I.fast_uniform((3, p["nz"], p["ny"], p["nx"]), seed=8, lo=-0.05,
+                       hi=0.05).astype(np.float32)
+    u[:, solid == 1] = 0.0
+    g.set_velocity(u)
+    o.set_velocity(u.astype(np.float64))
+    g.phase_update()
+    o.phase_update()
+    assert _rel(g.fields()[0], o.fields()[0]) < TOL_1STEP
+    g.volume_correct()
+    o.volume_correct()
+    gm, om = g.mass(), o.mass()
+    assert abs(gm["m_star"] - om["m_star"]) < 1e-5 * om["m_star"]
+    assert abs(gm["w_sum"] - om["w_sum"]) < 1e-5 * om["w_sum"]
+    assert _rel(g.fields()[0], o.fields()[0]) < TOL_1STEP
+
+
+@pytest.mark.parametrize("theta", [30.0, 90.0, 150.0])
+def test_one_step_full(theta):
+    p, solid, phi = _droplet_case(theta=theta)
+    u = np.zeros((3,) + phi.shape, np.float32)
+    u[0] = 0.01 * (phi > 0.5)
+    g, o = _pair(p, solid, phi, u)
+    g.step(1)
+    o.step(1)
+    gphi, gu, gp = g.fields()
+    ophi, ou, op = o.fields()
+    assert _rel(gphi, ophi) < TOL_1STEP
+    assert _rel(gu, ou) < TOL_1STEP
+    assert _rel(gp, op) < TOL_1STEP
+    fluid = solid == 0
+    assert _rel(g.populations()[:, fluid], o.populations()[:, fluid]) < TOL_1STEP
+
+
+def test_ragged_sizes_and_patterned_angles():
+    """Sizes that are not multiples of any tile, all three axes wrapping in
+    x and y, per-node contact angles."""
+    nx, ny, nz = 37, 13, 11
+    p = I.base_params(nx, ny, nz, sigma=0.02, theta_deg=70.0, rho_g=0.5)
+    solid = I.walls_z(nx, ny, nz)
+    solid[1:4, 5:8, 10:20] = 1  # a block on the floor
+    phi = I.droplet(nx, ny, nz, (18, 6, 3), 5.0, 4.0)
+    theta = (45.0 + 90.0 * I.fast_uniform((nz, ny, nx), seed=4)).astype(np.float32)
+    g, o = _pair(p, solid, phi, theta=theta)
+    g.step(3)
+    o.step(3)
+    gphi, gu, gp = g.fields()
+    ophi, ou, op = o.fields()
+    assert _rel(gphi, ophi) < 3 * TOL_1STEP
+    assert _rel(gu, ou) < 3 * TOL_1STEP
+
+
+def test_no_walls_fully_periodic():
+    n = 16
+    p = I.base_params(n, n, n, periodic=(1, 1, 1), sigma=0.01)
+    solid = np.zeros((n, n, n), np.uint8)
+    phi = I.droplet(n, n, n, (8, 8, 8), 5.0, 4.0)
+    g, o = _pair(p, solid, phi)
+    assert g.wall_list()["idx"].size == 0
+    g.step(5)
+    o.step(5)
+    assert _rel(g.fields()[0], o.fields()[0]) < 1e-5
+    assert _rel(g.fields()[1], o.fields()[1]) < 1e-4
+
+
+def test_two_dimensional_slab_config():
+    """The 2D static droplet (128 x 64, periodic in x, walls at y = 0 and
+    y = 63) as a D3Q27 slab one node thick, against the oracle's D3Q27 slab
+    and its D2Q9 run."""
+    p2, solid, phi = I.static_droplet_2d(60.0)
+    p3 = dict(p2, dim=3)
+    g, o3 = _pair(p3, solid, phi)
+    o2 = O.Oracle(p2)
+    o2.set_geometry(solid)
+    o2.set_fields(phi.astype(np.float64))
+    g.step(200)
+    o3.step(200)
+    o2.step(200)
+    assert _rel(g.fields()[0], o3.fields()[0]) < 1e-4
+    assert _rel(g.fields()[0], o2.fields()[0]) < 1e-4
+
+
+def test_thousand_steps_phi():
+    nx, ny, nz = 24, 24, 20
+    p = I.base_params(nx, ny, nz, sigma=0.01, rho_l=1.0, rho_g=0.1, nu_l=0.05,
+                      nu_g=0.1, theta_deg=60.0)
+    solid = I.walls_z(nx, ny, nz)
+    phi = I.droplet(nx, ny, nz, (12, 12, 0.5), 7.0, 4.0)
+    g, o = _pair(p, solid, phi)
+    g.step(1000)
+    o.step(1000)
+    gphi, ophi = g.fields()[0], o.fields()[0]
+    assert _rel(gphi, ophi) < 1e-3
+    m0 = o.mass()["m_ref"]
+    assert abs(g.mass()["m_ref"] - m0) < 1e-9 * m0
+
+
+def test_mass_held_and_deterministic():
+    p, solid, phi = _droplet_case(nx=40, ny=36, nz=30, theta=40.0)
+    runs = []
+    for _ in range(2):
+        g = _solver(p)
+        g.set_geometry(solid)
+        g.set_fields(phi)
+        g.step(50)
+        runs.append((g.fields()[0], g.mass()))
+    assert np.array_equal(runs[0][0], runs[1][0])
+    fphi = runs[0][0].astype(np.float64)
+    m = fphi[solid == 0].sum()
+    m_ref = runs[0][1]["m_ref"]
+    assert abs(m - m_ref) < 1e-8 * m_ref
+
+
+def test_state_errors():
+    from paper_2607_25444_b300 import cacl
+    p, solid, phi = _droplet_case()
+    g = _solver(p)
+    with pytest.raises(cacl.CaclError):
+        g.step(1)
+    with pytest.raises(cacl.CaclError):
+        g.set_fields(phi)
+    g.set_geometry(solid)
+    g.set_fields(phi)
+    with pytest.raises(cacl.CaclError):
+        g.step(-1)
+    bad = phi.copy()
+    bad[5, 5, 5] = np.nan
+    g.set_phi(bad)
+    with pytest.raises(cacl.CaclError):
+        g.check_finite()
