@@ -183,18 +183,20 @@ def run_reference(args):
 
 
 def time_lb_kernel(solver, torch, reps):
-    """Average duration of one collide-stream launch (CUDA events on the
-    library's stream, which is torch's current stream)."""
+    """Average duration of one collide-stream launch: reps launches enqueued
+    back to back between two CUDA events on the library's stream (torch's
+    current stream)."""
     stream = torch.cuda.current_stream()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    solver.lb_collide()
     torch.cuda.synchronize()
-    for i in range(reps):
-        starts[i].record(stream)
+    start.record(stream)
+    for _ in range(reps):
         solver.lb_collide()
-        ends[i].record(stream)
+    end.record(stream)
     torch.cuda.synchronize()
-    return float(np.mean([s.elapsed_time(e) for s, e in zip(starts, ends)])) / 1e3
+    return start.elapsed_time(end) / reps / 1e3
 
 
 def run_cuda(args):
@@ -210,7 +212,7 @@ def run_cuda(args):
 
     # a dedicated stream: the library and the CUDA events share it
     torch.cuda.set_stream(torch.cuda.Stream())
-    p, solid, phi = workload()
+    p, solid, phi = workload(args.grid)
     N = phi.size
     fluid = int((solid == 0).sum())
     s = cacl.Solver(p)
@@ -287,10 +289,11 @@ def run_cuda(args):
         "ms_per_step": dt_max / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "static droplet on a flat wall, 256^3, R0=40, "
+        "config": {"workload": f"static droplet on a flat wall, "
+                               f"{args.grid}^3, R0={40 * args.grid // 256}, "
                                "theta=60 deg, equal densities, nu=0.04, "
                                "sigma=0.02, W=4, D=0.02",
-                   "grid": [GRID, GRID, GRID], "storage": "f32",
+                   "grid": [args.grid] * 3, "storage": "f32",
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (populations 2 x 1.8 GB)",
                    "wall_nodes": W, "fluid_nodes": fluid},
@@ -319,6 +322,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--grid", type=int, default=GRID,
+                    help="cube edge (the benchmark is 256; smaller edges are "
+                         "for profiling captures)")
     ap.add_argument("--no-cpu", action="store_true",
                     help="skip the CPU-oracle baseline leg")
     args = ap.parse_args()

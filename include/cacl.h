@@ -138,9 +138,10 @@ cacl_status cacl_set_mass_ref(cacl_ctx* ctx, double m_ref);
 cacl_status cacl_step(cacl_ctx* ctx, int nsteps);
 
 /* The four parts of one step, enqueued singly (for inspection and part by
- * part checks). cacl_lb_collide reads phi and writes populations and u;
- * cacl_phase_update writes phi* and the block partial sums; cacl_volume_
- * correct forms lambda and phi^{n+1} = phi* + lambda chi(phi*). */
+ * part checks). cacl_lb_collide reads phi and writes populations, u and the
+ * compressive vector of phi; cacl_phase_update forms that vector from the
+ * current phi itself, then writes phi* and the block partial sums;
+ * cacl_volume_correct forms lambda and phi^{n+1} = phi* + lambda chi(phi*). */
 cacl_status cacl_ghost_update(cacl_ctx* ctx);
 cacl_status cacl_lb_collide(cacl_ctx* ctx);
 cacl_status cacl_phase_update(cacl_ctx* ctx);
@@ -167,6 +168,13 @@ cacl_status cacl_get_mass(cacl_ctx* ctx, double* m_ref, double* m_star,
 
 /* Returns CACL_ERR_DIVERGED if phi or u holds a NaN or Inf. Synchronises. */
 cacl_status cacl_check_finite(cacl_ctx* ctx);
+
+/* Launch-shape options (results do not depend on them beyond rounding
+ * order). CACL_OPT_PHASE_TILE selects the tile of the phase update:
+ * 0 = 32x16 nodes x 16 planes, 1 = 32x8 x 16, 2 = 32x8 x 32,
+ * 3 = 32x16 x 32. Returns CACL_ERR_ARG for an unknown option or value. */
+typedef enum { CACL_OPT_PHASE_TILE = 1 } cacl_option;
+cacl_status cacl_set_option(cacl_ctx* ctx, int option, int value);
 
 /* Grid size N and bytes of device memory the context holds. */
 cacl_status cacl_get_info(const cacl_ctx* ctx, int64_t* nodes,

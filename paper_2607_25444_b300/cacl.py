@@ -26,8 +26,9 @@ EXPORTS = (
     "cacl_ghost_update", "cacl_lb_collide", "cacl_phase_update",
     "cacl_volume_correct", "cacl_get_fields", "cacl_get_populations",
     "cacl_get_wall_list", "cacl_get_mass", "cacl_check_finite",
-    "cacl_get_info",
+    "cacl_set_option", "cacl_get_info",
 )
+OPT_PHASE_TILE = 1
 
 
 class CaclError(RuntimeError):
@@ -84,6 +85,7 @@ def load():
     L.cacl_get_wall_list.argtypes = [vp, vp, vp, vp, vp, C.POINTER(C.c_int32)]
     dp = C.POINTER(C.c_double)
     L.cacl_get_mass.argtypes = [vp, dp, dp, dp, dp]
+    L.cacl_set_option.argtypes = [vp, C.c_int, C.c_int]
     L.cacl_get_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int32)]
     for name in EXPORTS:
@@ -257,6 +259,9 @@ class Solver:
 
     def check_finite(self):
         self._check(self.L.cacl_check_finite(self.h))
+
+    def set_option(self, option, value):
+        self._check(self.L.cacl_set_option(self.h, int(option), int(value)))
 
     def info(self):
         n, b, w = C.c_int64(), C.c_int64(), C.c_int32()

@@ -155,6 +155,8 @@ cacl_status cacl_create(const cacl_params* p, void* stream, cacl_ctx** out) {
   }
   if ((e = cudaMalloc(&c->u, sizeof(float) * 3 * N)) != cudaSuccess)
     return bail("alloc u");
+  if ((e = cudaMalloc(&c->a, sizeof(float) * 3 * N)) != cudaSuccess)
+    return bail("alloc a");
   if ((e = cudaMalloc(&c->flags, N)) != cudaSuccess) return bail("alloc flags");
   c->part_blocks = phase_blocks(c);
   const int pb = std::max(c->part_blocks, mass_ref_blocks(N));
@@ -169,7 +171,7 @@ cacl_status cacl_create(const cacl_params* p, void* stream, cacl_ctx** out) {
     return bail("memset");
   if ((e = cudaMemsetAsync(c->flags, 0, N, c->stream)) != cudaSuccess)
     return bail("memset");
-  c->device_bytes = 2 * (int64_t)fbytes + 2 * 4 * N + 12 * N + N +
+  c->device_bytes = 2 * (int64_t)fbytes + 2 * 4 * N + 24 * N + N +
                     16 * (int64_t)pb + (int64_t)sizeof(MassScalars);
   *out = c;
   return CACL_OK;
@@ -179,7 +181,7 @@ void cacl_destroy(cacl_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graphs(c);
-  void* bufs[] = {c->f[0], c->f[1], c->phi[0], c->phi[1], c->u, c->flags,
+  void* bufs[] = {c->f[0], c->f[1], c->phi[0], c->phi[1], c->u, c->a, c->flags,
                   c->w_idx, c->w_donor, c->w_q, c->w_n6, c->w_nw, c->w_cot,
                   c->w_theta, c->w_g, c->partials, c->mass, c->scan_scratch,
                   c->bad_flag};
@@ -241,6 +243,7 @@ cacl_status cacl_set_fields(cacl_ctx* c, const float* phi, const float* u) {
                        c->stream), "upload u");
   else
     CK(cudaMemsetAsync(c->u, 0, sizeof(float) * 3 * N, c->stream), "zero u");
+  CK(cudaMemsetAsync(c->a, 0, sizeof(float) * 3 * N, c->stream), "zero a");
   CK(launch_init_populations(c), "init populations");
   CK(launch_mass_ref(c, c->phi[0]), "mass reference");
   CK(cudaStreamSynchronize(c->stream), "sync");
@@ -314,6 +317,7 @@ cacl_status cacl_lb_collide(cacl_ctx* c) {
 
 cacl_status cacl_phase_update(cacl_ctx* c) {
   if (!ready(c)) return c ? CACL_ERR_STATE : CACL_ERR_ARG;
+  CK(launch_compressive(c, c->phi[c->pcur]), "compressive vector");
   CK(launch_phase(c, c->phi[c->pcur], c->phi[1 - c->pcur]), "phase update");
   c->pcur ^= 1;
   return CACL_OK;
@@ -418,6 +422,17 @@ cacl_status cacl_check_finite(cacl_ctx* c) {
   CK(cudaStreamSynchronize(c->stream), "sync");
   if (bad) return fail(c, CACL_ERR_DIVERGED, "non-finite phi or u");
   return CACL_OK;
+}
+
+cacl_status cacl_set_option(cacl_ctx* c, int option, int value) {
+  if (!c) return CACL_ERR_ARG;
+  if (option == CACL_OPT_PHASE_TILE) {
+    if (value < 0 || value > 3) return fail(c, CACL_ERR_ARG, "unknown phase tile");
+    if (c->phase_variant != value) drop_graphs(c);
+    c->phase_variant = value;
+    return CACL_OK;
+  }
+  return fail(c, CACL_ERR_ARG, "unknown option");
 }
 
 cacl_status cacl_get_info(const cacl_ctx* c, int64_t* nodes,

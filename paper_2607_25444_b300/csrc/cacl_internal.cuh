@@ -51,6 +51,46 @@ __device__ __forceinline__ int wrap(int i, int d, int n) {
   return (j >= n) ? j - n : j;
 }
 
+// Isotropic gradient (Eq. grad_iso) and the neighbour sum of Eq. lap_iso of
+// phi at a node whose wrapped neighbour offsets are xo/yo/zo[0..2] (-1, 0,
+// +1), summed over pairs of opposite links. lap = 6 (ssum - (1 - w_0) phi).
+__device__ __forceinline__ void phi_stencil(const float* __restrict__ phi,
+                                            const int (&xo)[3],
+                                            const int (&yo)[3],
+                                            const int64_t (&zo)[3], float& gx,
+                                            float& gy, float& gz,
+                                            float& ssum) {
+  gx = 0.f;
+  gy = 0.f;
+  gz = 0.f;
+  ssum = 0.f;
+#pragma unroll
+  for (int q = 0; q < REST; ++q) {
+    const float vp = __ldg(phi + xo[1 + cx(q)] + yo[1 + cy(q)] + zo[1 + cz(q)]);
+    const float vm = __ldg(phi + xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)]);
+    const float dv = (3.0f * wq(q)) * (vp - vm);
+    gx += cx(q) * dv;
+    gy += cy(q) * dv;
+    gz += cz(q) * dv;
+    ssum += wq(q) * (vp + vm);
+  }
+}
+
+// Compressive vector a = phi (1 - phi) grad phi / |grad phi| (Sect. 2.2),
+// zero where |grad phi| < 1e-12.
+__device__ __forceinline__ void compressive(float phi0, float gx, float gy,
+                                            float gz, float& ax, float& ay,
+                                            float& az) {
+  const float g2 = gx * gx + gy * gy + gz * gz;
+  ax = ay = az = 0.f;
+  if (g2 >= 1e-24f) {
+    const float sc = phi0 * (1.0f - phi0) * rsqrtf(g2);
+    ax = sc * gx;
+    ay = sc * gy;
+    az = sc * gz;
+  }
+}
+
 // Scalar parameters uploaded once per context.
 struct Consts {
   float rho_g, drho;      // rho = rho_g + drho * phi
@@ -90,6 +130,7 @@ struct cacl_ctx {
   float* f[2] = {nullptr, nullptr};    // populations, [q][n], ping-pong
   float* phi[2] = {nullptr, nullptr};  // phi^n (with ghosts) and phi*
   float* u = nullptr;                  // [3][n]
+  float* a = nullptr;                  // [3][n] compressive vector of phi^n
   uint8_t* flags = nullptr;
   int fcur = 0;                         // buffer holding the current f*
   int pcur = 0;                         // buffer holding the current phi
@@ -104,6 +145,10 @@ struct cacl_ctx {
   float* w_cot = nullptr;   // cot(theta_c)
   float* w_theta = nullptr; // theta in degrees
   float* w_g = nullptr;     // ghost scratch
+
+  // kernel shape choices (cacl_set_option)
+  int phase_variant = 0;
+  int phase_nblocks = 0;   // blocks of the last phase-update launch
 
   // reductions
   int part_blocks = 0;
@@ -124,6 +169,7 @@ cudaError_t launch_geometry(cacl_ctx* c, const uint8_t* solid_dev);
 cudaError_t launch_ghost(cacl_ctx* c, float* phi);
 cudaError_t launch_lb(cacl_ctx* c, const float* fin, float* fout,
                       const float* phi);
+cudaError_t launch_compressive(cacl_ctx* c, const float* phi);
 cudaError_t phase_init_attributes();
 cudaError_t launch_phase(cacl_ctx* c, const float* phi_in, float* phi_out);
 cudaError_t launch_correct(cacl_ctx* c, float* phi);

@@ -6,7 +6,10 @@
 // One thread per node, x fastest. Populations are structure-of-arrays
 // f[q][n]; the pull reads f*_q(x - c_q) (halfway bounce-back f*_{opp q}(x)
 // when x - c_q is solid), the phi stencil is read through the read-only
-// cache, and the node writes its 27 post-collision populations and u.
+// cache, and the node writes its 27 post-collision populations, u, and the
+// compressive vector a = phi (1 - phi) grad phi / |grad phi| of the same
+// phi^n, which the phi update of this step needs at every node (Sect. 2.2):
+// the gradient is already in registers here.
 //
 // Collision algebra. With A2 = Pi - p* c_s^2 I - u u + (u a + a u)/2 (the
 // second moment of f - (f^eq - S/2), using sum f^eq c c = p* c_s^2 I + u u),
@@ -120,7 +123,8 @@ __device__ __forceinline__ void collide(const float (&f)[Q], float phi0,
 __global__ void __launch_bounds__(LB_BX * LB_BY)
 lb_collide_f32(const float* __restrict__ fin, float* __restrict__ fout,
                const float* __restrict__ phi, float* __restrict__ u,
-               const uint8_t* __restrict__ flags, Grid g, Consts k) {
+               float* __restrict__ a, const uint8_t* __restrict__ flags,
+               Grid g, Consts k) {
   const int x = blockIdx.x * LB_BX + threadIdx.x;
   const int y = blockIdx.y * LB_BY + threadIdx.y;
   const int z = blockIdx.z;
@@ -153,18 +157,14 @@ lb_collide_f32(const float* __restrict__ fin, float* __restrict__ fout,
 
   // isotropic gradient and Laplacian of phi (Eqs. grad_iso, lap_iso)
   const float phi0 = __ldg(phi + n);
-  float gx = 0.f, gy = 0.f, gz = 0.f, ssum = 0.f;
-#pragma unroll
-  for (int q = 0; q < REST; ++q) {
-    const float vp = __ldg(phi + xo[1 + cx(q)] + yo[1 + cy(q)] + zo[1 + cz(q)]);
-    const float vm = __ldg(phi + xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)]);
-    const float dv = (3.0f * wq(q)) * (vp - vm);
-    gx += cx(q) * dv;
-    gy += cy(q) * dv;
-    gz += cz(q) * dv;
-    ssum += wq(q) * (vp + vm);
-  }
+  float gx, gy, gz, ssum;
+  phi_stencil(phi, xo, yo, zo, gx, gy, gz, ssum);
   const float lap = 6.0f * (ssum - (1.0f - wq(REST)) * phi0);
+  float ax, ay, az;
+  compressive(phi0, gx, gy, gz, ax, ay, az);
+  a[n] = ax;
+  a[N + n] = ay;
+  a[2 * N + n] = az;
 
   NodeOut o;
   collide(f, phi0, gx, gy, gz, lap, k, o);
@@ -182,8 +182,8 @@ cudaError_t launch_lb(cacl_ctx* c, const float* fin, float* fout,
   const Grid g = c->g;
   dim3 block(LB_BX, LB_BY, 1);
   dim3 grid((g.nx + LB_BX - 1) / LB_BX, (g.ny + LB_BY - 1) / LB_BY, g.nz);
-  lb_collide_f32<<<grid, block, 0, c->stream>>>(fin, fout, phi, c->u, c->flags,
-                                                g, c->k);
+  lb_collide_f32<<<grid, block, 0, c->stream>>>(fin, fout, phi, c->u, c->a,
+                                                c->flags, g, c->k);
   return cudaGetLastError();
 }
 

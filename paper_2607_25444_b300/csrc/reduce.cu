@@ -158,8 +158,8 @@ int elem_blocks(int64_t N) { return (int)((N + ELEM_THREADS - 1) / ELEM_THREADS)
 }  // namespace
 
 cudaError_t launch_correct(cacl_ctx* c, float* phi) {
-  finalize_mass<<<1, FIN_THREADS, 0, c->stream>>>(c->partials, c->part_blocks,
-                                                 c->mass);
+  finalize_mass<<<1, FIN_THREADS, 0, c->stream>>>(c->partials,
+                                                 c->phase_nblocks, c->mass);
   const int64_t N = c->g.N;
   const int nb = (int)((N + 4 * ELEM_THREADS - 1) / (4 * ELEM_THREADS));
   correct_phi<<<nb, ELEM_THREADS, 0, c->stream>>>(phi, c->flags, c->mass, N,
