@@ -120,6 +120,9 @@ __device__ __forceinline__ void collide(const float (&f)[Q], float phi0,
   o.uz = uz;
 }
 
+// IDX is int when 27 N fits in 31 bits (every offset then needs one 32-bit
+// multiply-add and one widening address computation), int64_t otherwise.
+template <typename IDX>
 __global__ void __launch_bounds__(LB_BX * LB_BY)
 lb_collide_f32(const float* __restrict__ fin, float* __restrict__ fout,
                const float* __restrict__ phi, float* __restrict__ u,
@@ -129,36 +132,50 @@ lb_collide_f32(const float* __restrict__ fin, float* __restrict__ fout,
   const int y = blockIdx.y * LB_BY + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= g.nx || y >= g.ny) return;
-  const int64_t nxy = (int64_t)g.nx * g.ny;
-  const int64_t n = x + (int64_t)g.nx * y + nxy * z;
+  const IDX nx = g.nx;
+  const IDX nxy = (IDX)g.nx * g.ny;
+  const IDX N = (IDX)g.N;
+  const IDX n = x + nx * y + nxy * z;
   const uint8_t fl = flags[n];
   if (fl & FLAG_SOLID) return;
-  const int64_t N = g.N;
-  const int xo[3] = {wrap(x, -1, g.nx), x, wrap(x, 1, g.nx)};
-  const int yo[3] = {wrap(y, -1, g.ny) * g.nx, y * g.nx, wrap(y, 1, g.ny) * g.nx};
-  const int64_t zo[3] = {wrap(z, -1, g.nz) * nxy, z * nxy, wrap(z, 1, g.nz) * nxy};
+  const IDX xo[3] = {(IDX)wrap(x, -1, g.nx), (IDX)x, (IDX)wrap(x, 1, g.nx)};
+  const IDX yo[3] = {wrap(y, -1, g.ny) * nx, y * nx, wrap(y, 1, g.ny) * nx};
+  const IDX zo[3] = {wrap(z, -1, g.nz) * nxy, z * nxy, wrap(z, 1, g.nz) * nxy};
+  IDX yz[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) yz[b][c] = yo[b] + zo[c];
 
   float f[Q];
   if (fl & FLAG_NEAR) {
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const int64_t src = xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)];
+      const IDX src = xo[1 - cx(q)] + yz[1 - cy(q)][1 - cz(q)];
       const bool bb = (q != REST) && (__ldg(flags + src) & FLAG_SOLID);
-      f[q] = bb ? __ldg(fin + (int64_t)opp(q) * N + n)
-                : __ldg(fin + (int64_t)q * N + src);
+      f[q] = bb ? __ldg(fin + (opp(q) * N + n)) : __ldg(fin + (q * N + src));
     }
   } else {
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const int64_t src = xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)];
-      f[q] = __ldg(fin + (int64_t)q * N + src);
+      const IDX src = xo[1 - cx(q)] + yz[1 - cy(q)][1 - cz(q)];
+      f[q] = __ldg(fin + (q * N + src));
     }
   }
 
   // isotropic gradient and Laplacian of phi (Eqs. grad_iso, lap_iso)
   const float phi0 = __ldg(phi + n);
-  float gx, gy, gz, ssum;
-  phi_stencil(phi, xo, yo, zo, gx, gy, gz, ssum);
+  float gx = 0.f, gy = 0.f, gz = 0.f, ssum = 0.f;
+#pragma unroll
+  for (int q = 0; q < REST; ++q) {
+    const float vp = __ldg(phi + (xo[1 + cx(q)] + yz[1 + cy(q)][1 + cz(q)]));
+    const float vm = __ldg(phi + (xo[1 - cx(q)] + yz[1 - cy(q)][1 - cz(q)]));
+    const float dv = (3.0f * wq(q)) * (vp - vm);
+    gx += cx(q) * dv;
+    gy += cy(q) * dv;
+    gz += cz(q) * dv;
+    ssum += wq(q) * (vp + vm);
+  }
   const float lap = 6.0f * (ssum - (1.0f - wq(REST)) * phi0);
   float ax, ay, az;
   compressive(phi0, gx, gy, gz, ax, ay, az);
@@ -169,7 +186,7 @@ lb_collide_f32(const float* __restrict__ fin, float* __restrict__ fout,
   NodeOut o;
   collide(f, phi0, gx, gy, gz, lap, k, o);
 #pragma unroll
-  for (int q = 0; q < Q; ++q) fout[(int64_t)q * N + n] = o.f[q];
+  for (int q = 0; q < Q; ++q) fout[q * N + n] = o.f[q];
   u[n] = o.ux;
   u[N + n] = o.uy;
   u[2 * N + n] = o.uz;
@@ -182,8 +199,12 @@ cudaError_t launch_lb(cacl_ctx* c, const float* fin, float* fout,
   const Grid g = c->g;
   dim3 block(LB_BX, LB_BY, 1);
   dim3 grid((g.nx + LB_BX - 1) / LB_BX, (g.ny + LB_BY - 1) / LB_BY, g.nz);
-  lb_collide_f32<<<grid, block, 0, c->stream>>>(fin, fout, phi, c->u, c->a,
-                                                c->flags, g, c->k);
+  if ((int64_t)Q * g.N < (int64_t)INT32_MAX)
+    lb_collide_f32<int><<<grid, block, 0, c->stream>>>(fin, fout, phi, c->u, c->a,
+                                                       c->flags, g, c->k);
+  else
+    lb_collide_f32<int64_t><<<grid, block, 0, c->stream>>>(
+        fin, fout, phi, c->u, c->a, c->flags, g, c->k);
   return cudaGetLastError();
 }
 
