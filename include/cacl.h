@@ -50,7 +50,9 @@ typedef enum {
   CACL_ERR_STATE = -3,     /* call out of the required order */
   CACL_ERR_GEOMETRY = -4,  /* non-periodic axis not closed by solid layers */
   CACL_ERR_DIVERGED = -5,  /* non-finite phi or u found by cacl_check_finite */
-  CACL_ERR_TIMEOUT = -6    /* reserved for bounded device waits */
+  CACL_ERR_TIMEOUT = -6,   /* reserved for bounded device waits */
+  CACL_ERR_TOO_LARGE = -7  /* size above the fixed scratch of an
+                              allocation-free entry point */
 } cacl_status;
 
 /* Storage of the populations; arithmetic is FP32 in every mode. */
@@ -179,6 +181,39 @@ cacl_status cacl_set_option(cacl_ctx* ctx, int option, int value);
 /* Grid size N and bytes of device memory the context holds. */
 cacl_status cacl_get_info(const cacl_ctx* ctx, int64_t* nodes,
                           int64_t* device_bytes, int32_t* wall_count);
+
+/*
+ * Allocation-free volume correction (the paper has no counterpart: this is
+ * a library service). Some callers cannot call cudaMalloc: a process whose
+ * device memory already belongs to another allocator's pool, a host that
+ * forbids device allocation once it is serving, or code that must not risk
+ * the implicit device synchronisation of cudaFree. This call corrects a
+ * phase field they own without allocating anything: its reduction scratch
+ * is a fixed 256 KiB array compiled into the library, held on every GPU
+ * that loads the library until the process exits.
+ *
+ *   phi     device, n floats, corrected in place at fluid nodes:
+ *           phi += lambda chi(phi), chi = phi (1 - phi) inside
+ *           (eps_phi, 1 - eps_phi), lambda = (m_ref - M*) / W (0 if W = 0),
+ *           M* and W the FP64 sums of phi and chi over fluid nodes
+ *   solid   device, n bytes, nonzero = solid (left untouched)
+ *   n       1 <= n <= 67,108,864 (4096 x 16384); larger n returns
+ *           CACL_ERR_TOO_LARGE before any work is enqueued
+ *   m_ref   target fluid mass; eps_phi in (0, 1/2)
+ *   out     device, 3 doubles (M*, W, lambda) or NULL
+ *   stream  cudaStream_t or NULL; the call enqueues and returns
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Every call shares the one scratch array, so
+ * calls that overlap on the GPU (other streams, other host threads) race;
+ * serialise them on one stream. Returns CACL_ERR_ARG for null pointers or
+ * invalid sizes, CACL_ERR_CUDA for a launch or set-up failure.
+ */
+cacl_status cacl_volume_correct_noalloc(float* phi, const uint8_t* solid,
+                                        int64_t n, double m_ref,
+                                        double eps_phi, double* out,
+                                        void* stream);
 
 #ifdef __cplusplus
 }

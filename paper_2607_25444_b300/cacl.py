@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(HERE, "libcacl.so")
 CACL_OK = 0
 STATUS = {0: "CACL_OK", -1: "CACL_ERR_ARG", -2: "CACL_ERR_CUDA",
           -3: "CACL_ERR_STATE", -4: "CACL_ERR_GEOMETRY",
-          -5: "CACL_ERR_DIVERGED", -6: "CACL_ERR_TIMEOUT"}
+          -5: "CACL_ERR_DIVERGED", -6: "CACL_ERR_TIMEOUT",
+          -7: "CACL_ERR_TOO_LARGE"}
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 
 EXPORTS = (
@@ -26,7 +27,7 @@ EXPORTS = (
     "cacl_ghost_update", "cacl_lb_collide", "cacl_phase_update",
     "cacl_volume_correct", "cacl_get_fields", "cacl_get_populations",
     "cacl_get_wall_list", "cacl_get_mass", "cacl_check_finite",
-    "cacl_set_option", "cacl_get_info",
+    "cacl_set_option", "cacl_get_info", "cacl_volume_correct_noalloc",
 )
 OPT_PHASE_TILE = 1
 
@@ -88,6 +89,8 @@ def load():
     L.cacl_set_option.argtypes = [vp, C.c_int, C.c_int]
     L.cacl_get_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int32)]
+    L.cacl_volume_correct_noalloc.argtypes = [vp, vp, C.c_int64, C.c_double,
+                                              C.c_double, vp, vp]
     for name in EXPORTS:
         f = getattr(L, name)
         if name not in ("cacl_destroy", "cacl_last_error"):
@@ -126,6 +129,27 @@ def make_params(d):
     st = d.get("storage", "f32")
     p.storage = STORAGE[st] if isinstance(st, str) else int(st)
     return p
+
+
+def volume_correct_noalloc(phi, solid, m_ref, eps_phi=1e-3, out=None,
+                           stream=None):
+    """Allocation-free volume correction of a phase field held in torch
+    CUDA tensors: ``phi`` (float32, corrected in place), ``solid`` (uint8,
+    nonzero = solid), ``out`` (float64, 3 values: M*, W, lambda) or None.
+    Enqueued on ``stream`` (default: torch's current stream)."""
+    L = load()
+    if not (phi.is_cuda and solid.is_cuda and phi.is_contiguous()
+            and solid.is_contiguous()):
+        raise ValueError("phi and solid must be contiguous CUDA tensors")
+    if phi.numel() != solid.numel():
+        raise ValueError("phi and solid differ in size")
+    s = current_stream() if stream is None else stream
+    rc = L.cacl_volume_correct_noalloc(
+        C.c_void_p(phi.data_ptr()), C.c_void_p(solid.data_ptr()),
+        int(phi.numel()), float(m_ref), float(eps_phi),
+        None if out is None else C.c_void_p(out.data_ptr()), C.c_void_p(s))
+    if rc != CACL_OK:
+        raise CaclError(rc, "cacl_volume_correct_noalloc")
 
 
 def current_stream():
