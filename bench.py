@@ -51,6 +51,29 @@ def workload(grid=GRID, theta=THETA):
     return p, solid, phi
 
 
+def kernel_traffic(fluid_nodes):
+    """DRAM bytes per collide-stream launch from the committed ncu summary,
+    scaled by fluid nodes; None when the kernel source changed since the
+    capture (its hash no longer matches)."""
+    import hashlib
+    import re
+    prof = os.path.join(ROOT, "profiles", "lb_collide_f32_static_droplet_128cube.md")
+    if not os.path.exists(prof):
+        return None
+    text = open(prof).read()
+    per = re.search(r"traffic_bytes_per_fluid_node:\s*([0-9.eE+-]+)", text)
+    sha = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    if not per or not sha:
+        return None
+    h = hashlib.sha256()
+    for f in ("lb.cu", "cacl_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2607_25444_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != sha.group(1):
+        return None
+    return float(per.group(1)) * fluid_nodes
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -299,9 +322,11 @@ def run_cuda(args):
                    "wall_nodes": W, "fluid_nodes": fluid},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "lb_collide_f32",
+                     "traffic": kernel_traffic(fluid),
+                     "kernel": "lb_collide_f32",
                      "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": lb_bytes,
+                     "kernel_bytes_per_fluid_node": LB_BYTES_FLUID + 12,
                      "launch_ms": lb_s * 1e3},
         "step_roofline": {"bytes_per_node": STEP_BYTES, "achieved": step_gbs,
                           "frac": step_gbs / peak,
