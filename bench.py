@@ -32,13 +32,24 @@ import numpy as np  # noqa: E402
 GRID = 256
 THETA = 60.0
 METRIC = "MLUPS (CAC-LB step, 256^3)"
-# Algorithmic bytes of the collide-stream per fluid node: 27 populations
-# read + written (FP32), phi read, u written (3 x FP32), flags read.
-LB_BYTES_FLUID = 27 * 4 * 2 + 4 + 12 + 1
+STORE_BYTES = {"f32": 4, "f16": 2, "bf16": 2}
 LB_BYTES_SOLID = 1
-# Algorithmic bytes of one whole step per node: collide-stream 233, phi
-# update (phi read, u read, phi* written, flags) 21, correction 9.
-STEP_BYTES = LB_BYTES_FLUID + (4 + 12 + 4 + 1) + (4 + 4 + 1)
+
+
+def lb_bytes_fluid(storage="f32"):
+    """Algorithmic bytes of the collide-stream per fluid node: 27 populations
+    read + written, phi read, u written (3 x FP32), flags read."""
+    return 27 * STORE_BYTES[storage] * 2 + 4 + 12 + 1
+
+
+def step_bytes(storage="f32"):
+    """Algorithmic bytes of one whole step per node: collide-stream, phi
+    update (phi read, u read, phi* written, flags) 21, correction 9."""
+    return lb_bytes_fluid(storage) + (4 + 12 + 4 + 1) + (4 + 4 + 1)
+
+
+LB_BYTES_FLUID = lb_bytes_fluid()
+STEP_BYTES = step_bytes()
 L2_BYTES = 126 * 1024 * 1024
 
 
@@ -236,6 +247,7 @@ def run_cuda(args):
     # a dedicated stream: the library and the CUDA events share it
     torch.cuda.set_stream(torch.cuda.Stream())
     p, solid, phi = workload(args.grid)
+    p["storage"] = args.storage
     N = phi.size
     fluid = int((solid == 0).sum())
     s = cacl.Solver(p)
@@ -276,10 +288,10 @@ def run_cuda(args):
     # dominant kernel: the collide-stream, timed alone
     reps = max(5, min(50, args.steps))
     lb_s = time_lb_kernel(s, torch, reps)
-    lb_bytes = fluid * LB_BYTES_FLUID + (N - fluid) * LB_BYTES_SOLID
+    lb_bytes = fluid * lb_bytes_fluid(args.storage) + (N - fluid) * LB_BYTES_SOLID
     peak, peak_kind = measured_peaks()
     achieved = lb_bytes / lb_s / 1e9
-    step_gbs = N * STEP_BYTES * args.steps / dt / 1e9
+    step_gbs = N * step_bytes(args.storage) * args.steps / dt / 1e9
 
     # end to end through the C ABI with pinned host buffers
     ph_host = torch.empty(N, dtype=torch.float32, pin_memory=True).numpy()
@@ -299,6 +311,34 @@ def run_cuda(args):
     d2h = (out_phi.nbytes + out_u.nbytes) / args.steps
     s.close()
 
+    # the same workload with 16-bit population storage (FP32 arithmetic)
+    mixed = {}
+    if args.storage == "f32" and not args.no_variants:
+        for st in ("f16", "bf16"):
+            pv = dict(p, storage=st)
+            sv = cacl.Solver(pv)
+            sv.set_geometry(solid)
+            sv.set_fields(phi)
+            sv.step(args.warmup)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sv.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dtv = e0.elapsed_time(e1) / 1e3
+            lbv = time_lb_kernel(sv, torch, reps)
+            lbytes = fluid * lb_bytes_fluid(st) + (N - fluid) * LB_BYTES_SOLID
+            sv.check_finite()
+            mixed[st] = {"value": N * args.steps / dtv / 1e6 * world,
+                         "ms_per_step": dtv / args.steps * 1e3,
+                         "speedup_vs_f32": dt / dtv,
+                         "lb_launch_ms": lbv * 1e3,
+                         "lb_frac": lbytes / lbv / 1e9 / peak,
+                         "step_frac": N * step_bytes(st) * args.steps / dtv / 1e9 / peak}
+            sv.close()
+
     if rank != 0:
         return
     cpu = None
@@ -311,32 +351,34 @@ def run_cuda(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt_max / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "storage": args.storage,
         "data": "synthetic",
         "config": {"workload": f"static droplet on a flat wall, "
                                f"{args.grid}^3, R0={40 * args.grid // 256}, "
                                "theta=60 deg, equal densities, nu=0.04, "
                                "sigma=0.02, W=4, D=0.02",
-                   "grid": [args.grid] * 3, "storage": "f32",
+                   "grid": [args.grid] * 3, "storage": args.storage,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (populations 2 x 1.8 GB)",
                    "wall_nodes": W, "fluid_nodes": fluid},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": kernel_traffic(fluid),
+                     "traffic": kernel_traffic(fluid) if args.storage == "f32" else None,
                      "kernel": "lb_collide_f32",
                      "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": lb_bytes,
-                     "kernel_bytes_per_fluid_node": LB_BYTES_FLUID + 12,
+                     "kernel_bytes_per_fluid_node": lb_bytes_fluid(args.storage) + 12,
                      "launch_ms": lb_s * 1e3},
-        "step_roofline": {"bytes_per_node": STEP_BYTES, "achieved": step_gbs,
-                          "frac": step_gbs / peak,
-                          "ideal_mlups": peak * 1e9 / STEP_BYTES / 1e6},
+        "step_roofline": {"bytes_per_node": step_bytes(args.storage),
+                          "achieved": step_gbs, "frac": step_gbs / peak,
+                          "ideal_mlups": peak * 1e9 / step_bytes(args.storage) / 1e6},
         "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": kernels_per_step * args.steps,
         "clocks": clk.summary(),
         "checks": {"mass_drift_rel": drift, "lambda": mass["lam"]},
         "cpu_baseline": cpu,
+        "mixed": mixed or None,
     }
     print(json.dumps(line), flush=True)
 
@@ -350,6 +392,10 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID,
                     help="cube edge (the benchmark is 256; smaller edges are "
                          "for profiling captures)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="population storage of the headline line")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the 16-bit storage timings")
     ap.add_argument("--no-cpu", action="store_true",
                     help="skip the CPU-oracle baseline leg")
     args = ap.parse_args()

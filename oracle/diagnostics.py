@@ -60,3 +60,31 @@ def centre_of_mass_z(phi, solid):
     z = np.arange(phi.shape[0])[:, None, None]
     m = np.where(solid == 0, phi, 0.0)
     return float((z * m).sum() / m.sum())
+
+
+def footprint_radius(phi, layer=1):
+    """r = sqrt(A / pi) with A the count of nodes with phi > 1/2 on a layer."""
+    area = 0
+    for row in phi[layer]:
+        for v in row:
+            if v > 0.5:
+                area += 1
+    return float(np.sqrt(area / np.pi))
+
+
+def max_extent(phi):
+    """Largest x-extent of phi > 1/2 over all (z, y) rows, from linearly
+    interpolated crossings."""
+    best = 0.0
+    nz, ny, nx = phi.shape
+    for z in range(nz):
+        for y in range(ny):
+            row = phi[z, y]
+            pos = []
+            for x in range(nx - 1):
+                a, b = row[x] - 0.5, row[x + 1] - 0.5
+                if a * b < 0.0:
+                    pos.append(x + a / (a - b))
+            if len(pos) >= 2:
+                best = max(best, max(pos) - min(pos))
+    return best

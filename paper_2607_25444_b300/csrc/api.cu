@@ -114,7 +114,9 @@ cacl_status cacl_create(const cacl_params* p, void* stream, cacl_ctx** out) {
       !(p->rho_g > 0) || !(p->nu_l > 0) || !(p->nu_g > 0) ||
       !(p->eps_phi > 0 && p->eps_phi < 0.5) || !(p->sigma >= 0))
     return CACL_ERR_ARG;
-  if (p->storage != CACL_F32) return CACL_ERR_ARG;
+  if (p->storage != CACL_F32 && p->storage != CACL_F16_SHIFTED &&
+      p->storage != CACL_BF16_SHIFTED)
+    return CACL_ERR_ARG;
   cacl_ctx* c = new cacl_ctx();
   c->p = *p;
   c->g = {p->nx, p->ny, p->nz, N};
@@ -147,7 +149,7 @@ cacl_status cacl_create(const cacl_params* p, void* stream, cacl_ctx** out) {
     c->own_stream = true;
   }
   if ((e = phase_init_attributes()) != cudaSuccess) return bail("attributes");
-  const size_t fbytes = sizeof(float) * (size_t)Q * N;
+  const size_t fbytes = storage_bytes(p->storage) * (size_t)Q * N;
   for (int i = 0; i < 2; ++i) {
     if ((e = cudaMalloc(&c->f[i], fbytes)) != cudaSuccess) return bail("alloc f");
     if ((e = cudaMalloc(&c->phi[i], sizeof(float) * N)) != cudaSuccess)
@@ -256,8 +258,19 @@ cacl_status cacl_set_fields(cacl_ctx* c, const float* phi, const float* u) {
 cacl_status cacl_set_populations(cacl_ctx* c, const float* f) {
   if (!c || !f) return fail(c, CACL_ERR_ARG, "null argument");
   if (!ready(c)) return CACL_ERR_STATE;
-  CK(cudaMemcpyAsync(c->f[c->fcur], f, sizeof(float) * Q * c->g.N,
-                     cudaMemcpyHostToDevice, c->stream), "upload f");
+  const size_t bytes = sizeof(float) * Q * c->g.N;
+  if (c->p.storage == CACL_F32) {
+    CK(cudaMemcpyAsync(c->f[c->fcur], f, bytes, cudaMemcpyHostToDevice,
+                       c->stream), "upload f");
+  } else {
+    float* tmp = nullptr;
+    CK(cudaMalloc(&tmp, bytes), "alloc f staging");
+    cudaError_t e = cudaMemcpyAsync(tmp, f, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_to_storage(c, tmp, c->f[c->fcur]);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload f");
+  }
   CK(cudaStreamSynchronize(c->stream), "sync");
   return CACL_OK;
 }
@@ -361,9 +374,23 @@ cacl_status cacl_get_fields(cacl_ctx* c, float* phi, float* u, float* pstar,
 cacl_status cacl_get_populations(cacl_ctx* c, float* f, int device_ptrs) {
   if (!ready(c)) return c ? CACL_ERR_STATE : CACL_ERR_ARG;
   if (!f) return fail(c, CACL_ERR_ARG, "null argument");
-  CK(cudaMemcpyAsync(f, c->f[c->fcur], sizeof(float) * Q * c->g.N,
-                     device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                     c->stream), "copy f");
+  const size_t bytes = sizeof(float) * Q * c->g.N;
+  if (c->p.storage == CACL_F32) {
+    CK(cudaMemcpyAsync(f, c->f[c->fcur], bytes,
+                       device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       c->stream), "copy f");
+  } else if (device_ptrs) {
+    CK(launch_from_storage(c, c->f[c->fcur], f), "decode f");
+  } else {
+    float* tmp = nullptr;
+    CK(cudaMalloc(&tmp, bytes), "alloc f staging");
+    cudaError_t e = launch_from_storage(c, c->f[c->fcur], tmp);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(f, tmp, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy f");
+  }
   if (!device_ptrs) CK(cudaStreamSynchronize(c->stream), "sync");
   return CACL_OK;
 }

@@ -6,6 +6,8 @@
 // (Sect. 2.1), c_s^2 = 1/3. Everything is derived from q at compile time.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,6 +34,39 @@ __host__ __device__ constexpr float wq(int q) {
        : csq(q) == 2 ? 1.0f / 54.0f
                      : 1.0f / 216.0f;
 }
+
+// Population storage. FP32 stores f_i. The 16-bit forms store the
+// weight-normalised deviation from the rest state, h_i = (f_i - w_i p*_ref)
+// / w_i with p*_ref = 0 (the pressure gauge of the initial state), rounded
+// to nearest even; 1/w_i is exact in FP32, so the scaling adds no rounding.
+// All arithmetic stays FP32.
+struct StoreF32 {
+  using T = float;
+  __device__ __forceinline__ static float decode(T v, int q) { return v; }
+  __device__ __forceinline__ static T encode(float v, int q) { return v; }
+};
+
+struct StoreF16 {
+  using T = __half;
+  __device__ __forceinline__ static float decode(T v, int q) {
+    return __half2float(v) * wq(q);
+  }
+  __device__ __forceinline__ static T encode(float v, int q) {
+    return __float2half_rn(v * (1.0f / wq(q)));
+  }
+};
+
+struct StoreBF16 {
+  using T = __nv_bfloat16;
+  __device__ __forceinline__ static float decode(T v, int q) {
+    return __bfloat162float(v) * wq(q);
+  }
+  __device__ __forceinline__ static T encode(float v, int q) {
+    return __float2bfloat16_rn(v * (1.0f / wq(q)));
+  }
+};
+
+inline size_t storage_bytes(int storage) { return storage == CACL_F32 ? 4 : 2; }
 
 // Node flags (one byte per node).
 constexpr uint8_t FLAG_SOLID = 1;  // node is solid
@@ -127,7 +162,8 @@ struct cacl_ctx {
   bool has_fields = false;
 
   // device state
-  float* f[2] = {nullptr, nullptr};    // populations, [q][n], ping-pong
+  void* f[2] = {nullptr, nullptr};     // populations, [q][n], ping-pong,
+                                        // in the storage type of p.storage
   float* phi[2] = {nullptr, nullptr};  // phi^n (with ghosts) and phi*
   float* u = nullptr;                  // [3][n]
   float* a = nullptr;                  // [3][n] compressive vector of phi^n
@@ -167,7 +203,7 @@ struct cacl_ctx {
 namespace cacl {
 cudaError_t launch_geometry(cacl_ctx* c, const uint8_t* solid_dev);
 cudaError_t launch_ghost(cacl_ctx* c, float* phi);
-cudaError_t launch_lb(cacl_ctx* c, const float* fin, float* fout,
+cudaError_t launch_lb(cacl_ctx* c, const void* fin, void* fout,
                       const float* phi);
 cudaError_t launch_compressive(cacl_ctx* c, const float* phi);
 cudaError_t phase_init_attributes();
@@ -175,7 +211,9 @@ cudaError_t launch_phase(cacl_ctx* c, const float* phi_in, float* phi_out);
 cudaError_t launch_correct(cacl_ctx* c, float* phi);
 cudaError_t launch_mass_ref(cacl_ctx* c, const float* phi);
 cudaError_t launch_init_populations(cacl_ctx* c);
-cudaError_t launch_pstar(cacl_ctx* c, const float* f, float* out);
+cudaError_t launch_pstar(cacl_ctx* c, const void* f, float* out);
+cudaError_t launch_to_storage(cacl_ctx* c, const float* src, void* dst);
+cudaError_t launch_from_storage(cacl_ctx* c, const void* src, float* dst);
 cudaError_t launch_check_finite(cacl_ctx* c, const float* phi, int* bad_dev);
 int phase_blocks(const cacl_ctx* c);
 int mass_ref_blocks(int64_t N);

@@ -122,9 +122,10 @@ __device__ __forceinline__ void collide(const float (&f)[Q], float phi0,
 
 // IDX is int when 27 N fits in 31 bits (every offset then needs one 32-bit
 // multiply-add and one widening address computation), int64_t otherwise.
-template <typename IDX>
+template <typename Store, typename IDX>
 __global__ void __launch_bounds__(LB_BX * LB_BY)
-lb_collide_f32(const float* __restrict__ fin, float* __restrict__ fout,
+lb_collide(const typename Store::T* __restrict__ fin,
+           typename Store::T* __restrict__ fout,
                const float* __restrict__ phi, float* __restrict__ u,
                float* __restrict__ a, const uint8_t* __restrict__ flags,
                Grid g, Consts k) {
@@ -153,13 +154,13 @@ lb_collide_f32(const float* __restrict__ fin, float* __restrict__ fout,
     for (int q = 0; q < Q; ++q) {
       const IDX src = xo[1 - cx(q)] + yz[1 - cy(q)][1 - cz(q)];
       const bool bb = (q != REST) && (__ldg(flags + src) & FLAG_SOLID);
-      f[q] = bb ? __ldg(fin + (opp(q) * N + n)) : __ldg(fin + (q * N + src));
+      f[q] = Store::decode(bb ? __ldg(fin + (opp(q) * N + n)) : __ldg(fin + (q * N + src)), q);
     }
   } else {
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const IDX src = xo[1 - cx(q)] + yz[1 - cy(q)][1 - cz(q)];
-      f[q] = __ldg(fin + (q * N + src));
+      f[q] = Store::decode(__ldg(fin + (q * N + src)), q);
     }
   }
 
@@ -186,25 +187,35 @@ lb_collide_f32(const float* __restrict__ fin, float* __restrict__ fout,
   NodeOut o;
   collide(f, phi0, gx, gy, gz, lap, k, o);
 #pragma unroll
-  for (int q = 0; q < Q; ++q) fout[q * N + n] = o.f[q];
+  for (int q = 0; q < Q; ++q) fout[q * N + n] = Store::encode(o.f[q], q);
   u[n] = o.ux;
   u[N + n] = o.uy;
   u[2 * N + n] = o.uz;
 }
 
-}  // namespace
-
-cudaError_t launch_lb(cacl_ctx* c, const float* fin, float* fout,
-                      const float* phi) {
+template <typename Store>
+void launch_store(cacl_ctx* c, const void* fin, void* fout, const float* phi) {
+  using T = typename Store::T;
   const Grid g = c->g;
   dim3 block(LB_BX, LB_BY, 1);
   dim3 grid((g.nx + LB_BX - 1) / LB_BX, (g.ny + LB_BY - 1) / LB_BY, g.nz);
   if ((int64_t)Q * g.N < (int64_t)INT32_MAX)
-    lb_collide_f32<int><<<grid, block, 0, c->stream>>>(fin, fout, phi, c->u, c->a,
-                                                       c->flags, g, c->k);
+    lb_collide<Store, int><<<grid, block, 0, c->stream>>>(
+        (const T*)fin, (T*)fout, phi, c->u, c->a, c->flags, g, c->k);
   else
-    lb_collide_f32<int64_t><<<grid, block, 0, c->stream>>>(
-        fin, fout, phi, c->u, c->a, c->flags, g, c->k);
+    lb_collide<Store, int64_t><<<grid, block, 0, c->stream>>>(
+        (const T*)fin, (T*)fout, phi, c->u, c->a, c->flags, g, c->k);
+}
+
+}  // namespace
+
+cudaError_t launch_lb(cacl_ctx* c, const void* fin, void* fout,
+                      const float* phi) {
+  switch (c->p.storage) {
+    case CACL_F16_SHIFTED: launch_store<StoreF16>(c, fin, fout, phi); break;
+    case CACL_BF16_SHIFTED: launch_store<StoreBF16>(c, fin, fout, phi); break;
+    default: launch_store<StoreF32>(c, fin, fout, phi); break;
+  }
   return cudaGetLastError();
 }
 

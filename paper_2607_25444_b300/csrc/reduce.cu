@@ -107,10 +107,11 @@ fluid_sum(const float* __restrict__ phi, const uint8_t* __restrict__ flags,
 
 // f = f^eq(p* = 0, u) (Eq. feq3) into both population buffers; u = 0 at
 // solid nodes.
+template <typename Store>
 __global__ void __launch_bounds__(ELEM_THREADS)
-init_populations(float* __restrict__ f0, float* __restrict__ f1,
-                 float* __restrict__ u, const uint8_t* __restrict__ flags,
-                 int64_t N) {
+init_populations(typename Store::T* __restrict__ f0,
+                 typename Store::T* __restrict__ f1, float* __restrict__ u,
+                 const uint8_t* __restrict__ flags, int64_t N) {
   const int64_t n = (int64_t)blockIdx.x * ELEM_THREADS + threadIdx.x;
   if (n >= N) return;
   float ux = u[n], uy = u[N + n], uz = u[2 * N + n];
@@ -126,20 +127,45 @@ init_populations(float* __restrict__ f0, float* __restrict__ f1,
     const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
     const float v = wq(q) * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu +
                              4.5f * cu * (cu * cu - uu));
-    f0[(int64_t)q * N + n] = v;
-    f1[(int64_t)q * N + n] = v;
+    f0[(int64_t)q * N + n] = Store::encode(v, q);
+    f1[(int64_t)q * N + n] = Store::encode(v, q);
   }
 }
 
+template <typename Store>
 __global__ void __launch_bounds__(ELEM_THREADS)
-pstar_kernel(const float* __restrict__ f, const uint8_t* __restrict__ flags,
-             int64_t N, float* __restrict__ out) {
+pstar_kernel(const typename Store::T* __restrict__ f,
+             const uint8_t* __restrict__ flags, int64_t N,
+             float* __restrict__ out) {
   const int64_t n = (int64_t)blockIdx.x * ELEM_THREADS + threadIdx.x;
   if (n >= N) return;
   float s = 0.f;
 #pragma unroll
-  for (int q = 0; q < Q; ++q) s += f[(int64_t)q * N + n];
+  for (int q = 0; q < Q; ++q) s += Store::decode(f[(int64_t)q * N + n], q);
   out[n] = (flags[n] & FLAG_SOLID) ? 0.f : s;
+}
+
+// FP32 populations [q][n] <-> the storage type.
+template <typename Store>
+__global__ void __launch_bounds__(ELEM_THREADS)
+to_storage(const float* __restrict__ src, typename Store::T* __restrict__ dst,
+           int64_t N) {
+  const int64_t n = (int64_t)blockIdx.x * ELEM_THREADS + threadIdx.x;
+  if (n >= N) return;
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    dst[(int64_t)q * N + n] = Store::encode(src[(int64_t)q * N + n], q);
+}
+
+template <typename Store>
+__global__ void __launch_bounds__(ELEM_THREADS)
+from_storage(const typename Store::T* __restrict__ src, float* __restrict__ dst,
+             int64_t N) {
+  const int64_t n = (int64_t)blockIdx.x * ELEM_THREADS + threadIdx.x;
+  if (n >= N) return;
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    dst[(int64_t)q * N + n] = Store::decode(src[(int64_t)q * N + n], q);
 }
 
 __global__ void __launch_bounds__(ELEM_THREADS)
@@ -179,15 +205,38 @@ int mass_ref_blocks(int64_t N) {
   return (int)((N + ELEM_THREADS * 8 - 1) / (ELEM_THREADS * 8));
 }
 
+#define CACL_STORAGE_DISPATCH(c, KERNEL_CALL)                     \
+  switch ((c)->p.storage) {                                       \
+    case CACL_F16_SHIFTED: { using S = StoreF16; KERNEL_CALL; } break;  \
+    case CACL_BF16_SHIFTED: { using S = StoreBF16; KERNEL_CALL; } break; \
+    default: { using S = StoreF32; KERNEL_CALL; } break;          \
+  }
+
 cudaError_t launch_init_populations(cacl_ctx* c) {
-  init_populations<<<elem_blocks(c->g.N), ELEM_THREADS, 0, c->stream>>>(
-      c->f[0], c->f[1], c->u, c->flags, c->g.N);
+  const int nb = elem_blocks(c->g.N);
+  CACL_STORAGE_DISPATCH(c, (init_populations<S><<<nb, ELEM_THREADS, 0, c->stream>>>(
+      (S::T*)c->f[0], (S::T*)c->f[1], c->u, c->flags, c->g.N)));
   return cudaGetLastError();
 }
 
-cudaError_t launch_pstar(cacl_ctx* c, const float* f, float* out) {
-  pstar_kernel<<<elem_blocks(c->g.N), ELEM_THREADS, 0, c->stream>>>(
-      f, c->flags, c->g.N, out);
+cudaError_t launch_pstar(cacl_ctx* c, const void* f, float* out) {
+  const int nb = elem_blocks(c->g.N);
+  CACL_STORAGE_DISPATCH(c, (pstar_kernel<S><<<nb, ELEM_THREADS, 0, c->stream>>>(
+      (const S::T*)f, c->flags, c->g.N, out)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_storage(cacl_ctx* c, const float* src, void* dst) {
+  const int nb = elem_blocks(c->g.N);
+  CACL_STORAGE_DISPATCH(c, (to_storage<S><<<nb, ELEM_THREADS, 0, c->stream>>>(
+      src, (S::T*)dst, c->g.N)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_storage(cacl_ctx* c, const void* src, float* dst) {
+  const int nb = elem_blocks(c->g.N);
+  CACL_STORAGE_DISPATCH(c, (from_storage<S><<<nb, ELEM_THREADS, 0, c->stream>>>(
+      (const S::T*)src, dst, c->g.N)));
   return cudaGetLastError();
 }
 

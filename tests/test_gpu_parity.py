@@ -274,3 +274,63 @@ def test_phase_tile_variants(variant):
         o.volume_correct()
     assert _rel(g.fields()[0], o.fields()[0]) < TOL_1STEP
     assert abs(g.mass()["m_star"] - o.mass()["m_star"]) < 1e-6 * o.mass()["m_star"]
+
+
+def _quantize(f, storage):
+    """Round f_i / w_i to the 16-bit storage (nearest even) and scale back."""
+    import torch
+    c, w = O.lattice(3)
+    wv = w.reshape((27,) + (1,) * (f.ndim - 1)).astype(np.float32)
+    h = (f / wv).astype(np.float32)
+    if storage == "f16":
+        hq = h.astype(np.float16).astype(np.float32)
+    else:
+        hq = torch.from_numpy(h).to(torch.bfloat16).to(torch.float32).numpy()
+    return (hq * wv).astype(np.float32)
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 6e-4), ("bf16", 4.5e-3)])
+def test_reduced_storage_collide_parity(storage, tol):
+    """16-bit population storage with FP32 arithmetic: from populations that
+    the storage represents exactly, the moments and forces of one collide
+    match the oracle to FP32 round-off; the stored f* match to half an ulp
+    of the storage format (relative to the largest population)."""
+    p, solid, phi = _droplet_case()
+    p = dict(p, storage=storage)
+    g, o = _pair(p, solid, phi)
+    f = _quantize(I.random_state((p["nz"], p["ny"], p["nx"]), 27, seed=5,
+                                 amp=2e-3), storage)
+    g.set_populations(f)
+    o.set_populations(f.astype(np.float64))
+    assert np.array_equal(g.populations(), f)
+    g.lb_collide()
+    o.lb_collide()
+    fluid = solid == 0
+    assert _rel(g.fields()[1], o.fields()[1]) < TOL_1STEP
+    assert _rel(g.populations()[:, fluid], o.populations()[:, fluid]) < tol
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_reduced_storage_full_steps(storage):
+    """100 full steps with 16-bit storage stay close to the FP32 GPU run
+    and to the oracle in phi, hold mass, and are deterministic."""
+    p, solid, phi = _droplet_case(nx=32, ny=32, nz=24, theta=60.0)
+    runs = {}
+    for st in ("f32", storage, storage):
+        g = _solver(dict(p, storage=st))
+        g.set_geometry(solid)
+        g.set_fields(phi)
+        g.step(100)
+        runs.setdefault(st, []).append((g.fields()[0], g.mass()))
+    o = O.Oracle(p)
+    o.set_geometry(solid)
+    o.set_fields(phi.astype(np.float64))
+    o.step(100)
+    ref = o.fields()[0]
+    lo, hi = runs[storage]
+    assert np.array_equal(lo[0], hi[0])
+    bound = 2e-3 if storage == "f16" else 1e-2
+    assert _rel(lo[0], ref) < bound
+    assert _rel(runs["f32"][0][0], ref) < 1e-4
+    m = lo[0].astype(np.float64)[solid == 0].sum()
+    assert abs(m - lo[1]["m_ref"]) < 1e-8 * lo[1]["m_ref"]
