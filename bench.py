@@ -233,6 +233,73 @@ def time_lb_kernel(solver, torch, reps):
     return start.elapsed_time(end) / reps / 1e3
 
 
+def impact_sweep_cases(ncases=48, storage="f16"):
+    """Batched impact sweep shaped like the paper's Sect. 3.3: 48 cubes with
+    edges drawn from [64, 160], a drop of radius 0.2 n resting on the bottom
+    wall with a downward speed set by a Weber number drawn from [1, 80],
+    contact angle drawn from [120, 160] deg, density ratio 100, FP16
+    storage; seeded draws."""
+    import math as _m
+
+    from paper_2607_25444_b300 import inputs as I
+    out = []
+    for d in I.impact_sweep(ncases):
+        n = d["n"]
+        p = I.base_params(n, n, n, sigma=0.003, rho_l=1.0, rho_g=0.01,
+                          nu_l=0.03, nu_g=0.03, theta_deg=d["theta_deg"],
+                          storage=storage)
+        R = d["radius"]
+        solid = I.walls_z(n, n, n)
+        phi = I.droplet(n, n, n, (n / 2, n / 2, 0.5 + R + 1.0), R, p["width"])
+        u = np.zeros((3,) + phi.shape, np.float32)
+        u[2] = np.where(phi > 0.5, -d["u0"], 0.0)
+        out.append((p, solid, phi, u))
+        assert _m.isfinite(d["u0"])
+    return out
+
+
+def run_batched(args, torch, cacl, stream):
+    cases = impact_sweep_cases()
+    nodes = sum(c[2].size for c in cases)
+    b = cacl.Batch([c[0] for c in cases])
+    for view, (p, solid, phi, u) in zip(b.cases, cases):
+        view.set_geometry(solid)
+        view.set_fields(phi, u)
+    del cases
+    best = b.autotune(steps=2)
+    k = max(4, args.steps // 20)
+    b.step(2)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    # the same cases one after another, each as its own graph
+    e0.record(stream)
+    for view in b.cases:
+        view.step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_single = e0.elapsed_time(e1) / 1e3
+    finite = True
+    for view in b.cases:
+        try:
+            view.check_finite()
+        except cacl.CaclError:
+            finite = False
+    b.close()
+    return {"workload": "impact sweep, 48 cubes 64..160 (seeded), R = 0.2 n, "
+                        "theta 120..160 deg, We 1..80, density ratio 100, f16 storage",
+            "cases": 48, "nodes": nodes, "steps": k,
+            "value": nodes * k / t_batch / 1e6, "unit": "MLUPS",
+            "one_case_at_a_time": nodes * k / t_single / 1e6,
+            "speedup": t_single / t_batch, "autotuned": best,
+            "finite": finite}
+
+
 def run_cuda(args):
     import torch
     rank, world, local = dist_env()
@@ -339,6 +406,10 @@ def run_cuda(args):
                          "step_frac": N * step_bytes(st) * args.steps / dtv / 1e9 / peak}
             sv.close()
 
+    batched = None
+    if not args.no_batch and world == 1:
+        batched = run_batched(args, torch, cacl, stream)
+
     if rank != 0:
         return
     cpu = None
@@ -379,6 +450,7 @@ def run_cuda(args):
         "checks": {"mass_drift_rel": drift, "lambda": mass["lam"]},
         "cpu_baseline": cpu,
         "mixed": mixed or None,
+        "batched": batched,
     }
     print(json.dumps(line), flush=True)
 
@@ -394,6 +466,8 @@ def main():
                          "for profiling captures)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="population storage of the headline line")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched impact-sweep timing")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the 16-bit storage timings")
     ap.add_argument("--no-cpu", action="store_true",

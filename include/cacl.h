@@ -171,6 +171,45 @@ cacl_status cacl_get_mass(cacl_ctx* ctx, double* m_ref, double* m_star,
 /* Returns CACL_ERR_DIVERGED if phi or u holds a NaN or Inf. Synchronises. */
 cacl_status cacl_check_finite(cacl_ctx* ctx);
 
+/*
+ * Batches: many cases of uneven grid size advanced together (each stage of
+ * the step is one grid-strided launch over a work-list spanning all cases,
+ * the step is a captured CUDA graph). Every case is an ordinary context
+ * owned by the batch: set it up and query it with the single-case calls on
+ * the handle from cacl_batch_case (geometry, angles, fields, getters). All
+ * cases must use the same storage; they advance in lockstep, so do not step
+ * a case on its own between batch steps (cacl_batch_step then returns
+ * CACL_ERR_STATE). Giving a case a new geometry is picked up at the next
+ * cacl_batch_step.
+ */
+typedef struct cacl_batch cacl_batch;
+
+/* ncases >= 1 parameter sets (same storage); stream as for cacl_create. */
+cacl_status cacl_batch_create(const cacl_params* params, int ncases,
+                              void* stream, cacl_batch** out);
+void cacl_batch_destroy(cacl_batch* batch);
+const char* cacl_batch_last_error(const cacl_batch* batch);
+
+/* The batch's context of case i (0 <= i < ncases); owned by the batch. */
+cacl_status cacl_batch_case(cacl_batch* batch, int i, cacl_ctx** out);
+
+/* Advance every case by nsteps full steps (ghost update, collide-stream,
+ * phi update, volume correction with a per-case lambda). */
+cacl_status cacl_batch_step(cacl_batch* batch, int nsteps);
+
+/* Launch shapes of the batched stages: collide-stream rows of 64, 128 or
+ * 256 threads with a resident-sized grid striding through the work-list
+ * (lb_variant 0, 1, 2) or one block per row (3, 4, 5), and the phi-update
+ * tile (0..3, as CACL_OPT_PHASE_TILE). */
+cacl_status cacl_batch_set_option(cacl_batch* batch, int lb_variant,
+                                  int phase_variant);
+
+/* Autotuner: times `steps` batch steps for every launch-shape pair, keeps
+ * the fastest and returns it with its time per step. It runs real steps:
+ * every case advances by 25 * steps steps (use it as the warm-up). */
+cacl_status cacl_batch_autotune(cacl_batch* batch, int steps, int* lb_variant,
+                                int* phase_variant, float* best_ms);
+
 /* Launch-shape options (results do not depend on them beyond rounding
  * order). CACL_OPT_PHASE_TILE selects the tile of the phase update:
  * 0 = 32x16 nodes x 16 planes, 1 = 32x8 x 16, 2 = 32x8 x 32,

@@ -28,6 +28,9 @@ EXPORTS = (
     "cacl_volume_correct", "cacl_get_fields", "cacl_get_populations",
     "cacl_get_wall_list", "cacl_get_mass", "cacl_check_finite",
     "cacl_set_option", "cacl_get_info", "cacl_volume_correct_noalloc",
+    "cacl_batch_create", "cacl_batch_destroy", "cacl_batch_last_error",
+    "cacl_batch_case", "cacl_batch_step", "cacl_batch_set_option",
+    "cacl_batch_autotune",
 )
 OPT_PHASE_TILE = 1
 
@@ -91,9 +94,21 @@ def load():
                                 C.POINTER(C.c_int32)]
     L.cacl_volume_correct_noalloc.argtypes = [vp, vp, C.c_int64, C.c_double,
                                               C.c_double, vp, vp]
+    L.cacl_batch_create.argtypes = [C.POINTER(CaclParams), C.c_int, vp,
+                                    C.POINTER(vp)]
+    L.cacl_batch_destroy.argtypes = [vp]
+    L.cacl_batch_destroy.restype = None
+    L.cacl_batch_last_error.argtypes = [vp]
+    L.cacl_batch_last_error.restype = C.c_char_p
+    L.cacl_batch_case.argtypes = [vp, C.c_int, C.POINTER(vp)]
+    L.cacl_batch_step.argtypes = [vp, C.c_int]
+    L.cacl_batch_set_option.argtypes = [vp, C.c_int, C.c_int]
+    L.cacl_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int),
+                                      C.POINTER(C.c_int), C.POINTER(C.c_float)]
     for name in EXPORTS:
         f = getattr(L, name)
-        if name not in ("cacl_destroy", "cacl_last_error"):
+        if name not in ("cacl_destroy", "cacl_last_error", "cacl_batch_destroy",
+                        "cacl_batch_last_error"):
             f.restype = C.c_int
     _lib = L
     return L
@@ -166,8 +181,17 @@ class Solver:
     two-dimensional problem is a periodic slab one node thick).
     """
 
-    def __init__(self, params, stream=None):
+    def __init__(self, params, stream=None, handle=None):
         self.L = load()
+        if handle is not None:  # a case owned by a Batch
+            self.params = dict(params)
+            self.p = make_params(params)
+            self.shape = (self.p.nz, self.p.ny, self.p.nx)
+            self.N = self.p.nx * self.p.ny * self.p.nz
+            self.h = handle
+            self._owned = False
+            return
+        self._owned = True
         if params.get("dim", 3) != 3 and params.get("nz", 1) != 1:
             raise ValueError("dim 2 runs as a D3Q27 slab with nz = 1")
         self.params = dict(params)
@@ -183,7 +207,8 @@ class Solver:
 
     def close(self):
         if getattr(self, "h", None):
-            self.L.cacl_destroy(self.h)
+            if getattr(self, "_owned", True):
+                self.L.cacl_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -291,3 +316,57 @@ class Solver:
         n, b, w = C.c_int64(), C.c_int64(), C.c_int32()
         self._check(self.L.cacl_get_info(self.h, C.byref(n), C.byref(b), C.byref(w)))
         return dict(nodes=n.value, device_bytes=b.value, wall_count=w.value)
+
+
+class Batch:
+    """Many cases advanced together: each stage of the step is one launch
+    over all cases. ``cases[i]`` is a Solver view of case i for set-up and
+    queries (owned by the batch)."""
+
+    def __init__(self, params_list, stream=None):
+        self.L = load()
+        arr = (CaclParams * len(params_list))(*[make_params(p) for p in params_list])
+        s = current_stream() if stream is None else stream
+        h = C.c_void_p()
+        rc = self.L.cacl_batch_create(arr, len(params_list), C.c_void_p(s),
+                                      C.byref(h))
+        if rc != CACL_OK:
+            raise CaclError(rc, "cacl_batch_create failed")
+        self.h = h
+        self.cases = []
+        for i, p in enumerate(params_list):
+            ch = C.c_void_p()
+            self._check(self.L.cacl_batch_case(self.h, i, C.byref(ch)))
+            self.cases.append(Solver(p, handle=ch))
+
+    def _check(self, rc):
+        if rc != CACL_OK:
+            msg = self.L.cacl_batch_last_error(self.h)
+            raise CaclError(rc, msg.decode() if msg else "")
+
+    def step(self, n=1):
+        self._check(self.L.cacl_batch_step(self.h, int(n)))
+
+    def set_option(self, lb_variant, phase_variant):
+        self._check(self.L.cacl_batch_set_option(self.h, int(lb_variant),
+                                                 int(phase_variant)))
+
+    def autotune(self, steps=3):
+        lv, pv, ms = C.c_int(), C.c_int(), C.c_float()
+        self._check(self.L.cacl_batch_autotune(self.h, int(steps), C.byref(lv),
+                                               C.byref(pv), C.byref(ms)))
+        return dict(lb_variant=lv.value, phase_variant=pv.value,
+                    ms_per_step=ms.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            for c in self.cases:
+                c.h = None
+            self.L.cacl_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -223,6 +223,7 @@ cacl_status cacl_set_geometry(cacl_ctx* c, const uint8_t* solid) {
   if (e != cudaSuccess) return cuda_fail(c, e, "geometry");
   c->has_geometry = true;
   c->has_fields = false;
+  c->geom_version++;
   return upload_angles(c, nullptr);
 }
 

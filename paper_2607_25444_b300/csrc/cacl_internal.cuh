@@ -149,6 +149,82 @@ struct MassScalars {
   int pad;
 };
 
+// One case of a batch as the batched kernels see it: grid, constants and
+// the device buffers of the case's own context.
+struct CaseDesc {
+  Grid g;
+  Consts k;
+  void* f[2];
+  float* phi[2];
+  float* u;
+  float* a;
+  uint8_t* flags;
+  int W;
+  int32_t* w_idx;
+  int32_t* w_donor;
+  int8_t* w_q;
+  float* w_nw;
+  float* w_cot;
+  float* w_g;
+  double* partials;
+  MassScalars* mass;
+  int phase_nb;  // phase-update blocks of this case for the batch's tile
+};
+
+// Virtual block b of a work-list belongs to case c when
+// start[c] <= b < start[c + 1]; every thread of a block finds the same c.
+__device__ __forceinline__ int find_case(const int* __restrict__ start,
+                                         int ncases, int b) {
+  int lo = 0, hi = ncases - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Work-list of one batched stage: per-case starts of its virtual blocks.
+struct WorkList {
+  const int* start;  // device, ncases + 1
+  int ncases;
+  int total;
+};
+
+// A persistent block of a batched stage walks the virtual blocks of the
+// work-list in increasing order (a contiguous range [b0, b1), or every
+// gridDim.x-th block); the descriptor of the current case sits in shared
+// memory and is refreshed only when the walk crosses into a later case.
+// Every thread of the block must call seek() (it synchronises).
+struct CaseCursor {
+  CaseDesc d;
+  int c, cstart, cend;
+
+  __device__ __forceinline__ void begin() { cend = -1; }
+  // make the case of virtual block b current
+  __device__ __forceinline__ void seek(const CaseDesc* __restrict__ cases,
+                                       const WorkList& wl, int b) {
+    if (b < cend) return;  // uniform across the block: cend is shared
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      c = find_case(wl.start, wl.ncases, b);
+      cstart = __ldg(wl.start + c);
+      cend = __ldg(wl.start + c + 1);
+      d = cases[c];
+    }
+    __syncthreads();
+  }
+};
+
+__device__ __forceinline__ void block_range(const WorkList& wl, int& b0,
+                                            int& b1) {
+  const int per = (wl.total + (int)gridDim.x - 1) / (int)gridDim.x;
+  b0 = min((int)blockIdx.x * per, wl.total);
+  b1 = min(b0 + per, wl.total);
+}
+
 }  // namespace cacl
 
 struct cacl_ctx {
@@ -160,6 +236,7 @@ struct cacl_ctx {
   std::string err;
   bool has_geometry = false;
   bool has_fields = false;
+  int geom_version = 0;  // bumped by every cacl_set_geometry
 
   // device state
   void* f[2] = {nullptr, nullptr};     // populations, [q][n], ping-pong,
@@ -217,4 +294,26 @@ cudaError_t launch_from_storage(cacl_ctx* c, const void* src, float* dst);
 cudaError_t launch_check_finite(cacl_ctx* c, const float* phi, int* bad_dev);
 int phase_blocks(const cacl_ctx* c);
 int mass_ref_blocks(int64_t N);
+
+// Batched stages: one grid-strided launch runs the stage for every case of
+// a work-list; fc / pc select each case's current population / phi buffer.
+// collide-stream rows of 64, 128, 256 threads, persistent (variants 0-2)
+// or one block per row (3-5)
+constexpr int LB_BATCH_VARIANTS = 6;
+int lb_batch_row(int variant);
+bool lb_batch_persistent(int variant);
+cudaError_t launch_lb_batch(const CaseDesc* cases, WorkList wl, int storage,
+                            int variant, int grid, int fc, int pc,
+                            cudaStream_t st);
+int lb_batch_occupancy(int storage, int variant);
+cudaError_t launch_ghost_batch(const CaseDesc* cases, WorkList wl, int grid,
+                               int pc, cudaStream_t st);
+int ghost_batch_block();
+cudaError_t launch_phase_batch(const CaseDesc* cases, WorkList wl, int variant,
+                               int grid, int pc, cudaStream_t st);
+int phase_batch_occupancy(int variant);
+void phase_tile(int variant, int& ty, int& zc);
+cudaError_t launch_correct_batch(const CaseDesc* cases, int ncases, WorkList wl,
+                                 int grid, int pc, cudaStream_t st);
+int correct_batch_nodes();
 }  // namespace cacl

@@ -12,13 +12,13 @@ namespace {
 
 constexpr int GHOST_THREADS = 128;
 
-__global__ void __launch_bounds__(GHOST_THREADS)
-ghost_eval(const float* __restrict__ phi, const int32_t* __restrict__ donor,
-           const int8_t* __restrict__ qstar, const float* __restrict__ nw,
-           const float* __restrict__ cot_c, float* __restrict__ g_out, int W,
-           Grid g) {
-  const int w = blockIdx.x * GHOST_THREADS + threadIdx.x;
-  if (w >= W) return;
+__device__ __forceinline__ void ghost_one(int w, const float* __restrict__ phi,
+                                          const int32_t* __restrict__ donor,
+                                          const int8_t* __restrict__ qstar,
+                                          const float* __restrict__ nw,
+                                          const float* __restrict__ cot_c,
+                                          float* __restrict__ g_out, int W,
+                                          const Grid& g) {
   const int d = donor[w];
   const int x = d % g.nx;
   const int r = d / g.nx;
@@ -55,6 +55,49 @@ ghost_eval(const float* __restrict__ phi, const int32_t* __restrict__ donor,
 }
 
 __global__ void __launch_bounds__(GHOST_THREADS)
+ghost_eval(const float* __restrict__ phi, const int32_t* __restrict__ donor,
+           const int8_t* __restrict__ qstar, const float* __restrict__ nw,
+           const float* __restrict__ cot_c, float* __restrict__ g_out, int W,
+           Grid g) {
+  const int w = blockIdx.x * GHOST_THREADS + threadIdx.x;
+  if (w < W) ghost_one(w, phi, donor, qstar, nw, cot_c, g_out, W, g);
+}
+
+// Batched ghost pass: virtual block b covers GHOST_THREADS wall nodes of
+// its case. eval and scatter are separate launches (Jacobi semantics).
+__global__ void __launch_bounds__(GHOST_THREADS)
+ghost_eval_batch(const CaseDesc* __restrict__ cases, WorkList wl, int pc) {
+  __shared__ CaseCursor cur;
+  if (threadIdx.x == 0) cur.begin();
+  __syncthreads();
+  int b0, b1;
+  block_range(wl, b0, b1);
+  for (int b = b0; b < b1; ++b) {
+    cur.seek(cases, wl, b);
+    const CaseDesc& cd = cur.d;
+    const int w = (b - cur.cstart) * GHOST_THREADS + threadIdx.x;
+    if (w < cd.W)
+      ghost_one(w, cd.phi[pc], cd.w_donor, cd.w_q, cd.w_nw, cd.w_cot, cd.w_g,
+                cd.W, cd.g);
+  }
+}
+
+__global__ void __launch_bounds__(GHOST_THREADS)
+ghost_scatter_batch(const CaseDesc* __restrict__ cases, WorkList wl, int pc) {
+  __shared__ CaseCursor cur;
+  if (threadIdx.x == 0) cur.begin();
+  __syncthreads();
+  int b0, b1;
+  block_range(wl, b0, b1);
+  for (int b = b0; b < b1; ++b) {
+    cur.seek(cases, wl, b);
+    const CaseDesc& cd = cur.d;
+    const int w = (b - cur.cstart) * GHOST_THREADS + threadIdx.x;
+    if (w < cd.W) cd.phi[pc][cd.w_idx[w]] = cd.w_g[w];
+  }
+}
+
+__global__ void __launch_bounds__(GHOST_THREADS)
 ghost_scatter(float* __restrict__ phi, const int32_t* __restrict__ idx,
               const float* __restrict__ g_in, int W) {
   const int w = blockIdx.x * GHOST_THREADS + threadIdx.x;
@@ -62,6 +105,16 @@ ghost_scatter(float* __restrict__ phi, const int32_t* __restrict__ idx,
 }
 
 }  // namespace
+
+int ghost_batch_block() { return GHOST_THREADS; }
+
+cudaError_t launch_ghost_batch(const CaseDesc* cases, WorkList wl, int grid,
+                               int pc, cudaStream_t st) {
+  if (wl.total == 0) return cudaSuccess;
+  ghost_eval_batch<<<grid, GHOST_THREADS, 0, st>>>(cases, wl, pc);
+  ghost_scatter_batch<<<grid, GHOST_THREADS, 0, st>>>(cases, wl, pc);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ghost(cacl_ctx* c, float* phi) {
   const int W = c->wall_count;

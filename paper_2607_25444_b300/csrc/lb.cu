@@ -122,17 +122,16 @@ __device__ __forceinline__ void collide(const float (&f)[Q], float phi0,
 
 // IDX is int when 27 N fits in 31 bits (every offset then needs one 32-bit
 // multiply-add and one widening address computation), int64_t otherwise.
+// The node (x, y, z) of one grid: pull, stencil, collision, stores.
 template <typename Store, typename IDX>
-__global__ void __launch_bounds__(LB_BX * LB_BY)
-lb_collide(const typename Store::T* __restrict__ fin,
-           typename Store::T* __restrict__ fout,
-               const float* __restrict__ phi, float* __restrict__ u,
-               float* __restrict__ a, const uint8_t* __restrict__ flags,
-               Grid g, Consts k) {
-  const int x = blockIdx.x * LB_BX + threadIdx.x;
-  const int y = blockIdx.y * LB_BY + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= g.nx || y >= g.ny) return;
+__device__ __forceinline__ void lb_node(int x, int y, int z,
+                                        const typename Store::T* __restrict__ fin,
+                                        typename Store::T* __restrict__ fout,
+                                        const float* __restrict__ phi,
+                                        float* __restrict__ u,
+                                        float* __restrict__ a,
+                                        const uint8_t* __restrict__ flags,
+                                        const Grid& g, const Consts& k) {
   const IDX nx = g.nx;
   const IDX nxy = (IDX)g.nx * g.ny;
   const IDX N = (IDX)g.N;
@@ -193,6 +192,50 @@ lb_collide(const typename Store::T* __restrict__ fin,
   u[2 * N + n] = o.uz;
 }
 
+template <typename Store, typename IDX>
+__global__ void __launch_bounds__(LB_BX * LB_BY)
+lb_collide(const typename Store::T* __restrict__ fin,
+           typename Store::T* __restrict__ fout, const float* __restrict__ phi,
+           float* __restrict__ u, float* __restrict__ a,
+           const uint8_t* __restrict__ flags, Grid g, Consts k) {
+  const int x = blockIdx.x * LB_BX + threadIdx.x;
+  const int y = blockIdx.y * LB_BY + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return;
+  lb_node<Store, IDX>(x, y, z, fin, fout, phi, u, a, flags, g, k);
+}
+
+// Batched collide-stream: virtual block b of the work-list is row block
+// (bx, y, z) of its case; rows of BX threads along x. Blocks stride through
+// the work-list (b, b + gridDim.x, ...) so that the rows in flight at any
+// time are neighbours, as in a plain launch, and their phi stencils share
+// cache lines; the case changes every few thousand rows.
+// PERSIST: a resident-sized grid strides through the work-list; otherwise
+// one block per work item (the block scheduler does the distribution).
+template <typename Store, int BX, bool PERSIST>
+__global__ void __launch_bounds__(BX)
+lb_collide_batch(const CaseDesc* __restrict__ cases, WorkList wl, int fc,
+                 int pc) {
+  using T = typename Store::T;
+  __shared__ CaseCursor cur;
+  if (threadIdx.x == 0) cur.begin();
+  __syncthreads();
+  const int stride = PERSIST ? (int)gridDim.x : wl.total;
+  for (int b = blockIdx.x; b < wl.total; b += stride) {
+    cur.seek(cases, wl, b);
+    const CaseDesc& cd = cur.d;
+    const int nbx = (cd.g.nx + BX - 1) / BX;
+    const int local = b - cur.cstart;
+    const int bx = local % nbx;
+    const int row = local / nbx;
+    const int y = row % cd.g.ny, z = row / cd.g.ny;
+    const int x = bx * BX + threadIdx.x;
+    if (x < cd.g.nx)
+      lb_node<Store, int>(x, y, z, (const T*)cd.f[fc], (T*)cd.f[1 - fc],
+                          cd.phi[pc], cd.u, cd.a, cd.flags, cd.g, cd.k);
+  }
+}
+
 template <typename Store>
 void launch_store(cacl_ctx* c, const void* fin, void* fout, const float* phi) {
   using T = typename Store::T;
@@ -217,6 +260,49 @@ cudaError_t launch_lb(cacl_ctx* c, const void* fin, void* fout,
     default: launch_store<StoreF32>(c, fin, fout, phi); break;
   }
   return cudaGetLastError();
+}
+
+int lb_batch_row(int variant) {
+  const int r = variant % 3;
+  return r == 0 ? 64 : r == 2 ? 256 : 128;
+}
+
+bool lb_batch_persistent(int variant) { return variant < 3; }
+
+namespace {
+template <typename Store>
+void* lb_batch_fn(int variant) {
+  switch (variant) {
+    case 0: return (void*)lb_collide_batch<Store, 64, true>;
+    case 2: return (void*)lb_collide_batch<Store, 256, true>;
+    case 3: return (void*)lb_collide_batch<Store, 64, false>;
+    case 4: return (void*)lb_collide_batch<Store, 128, false>;
+    case 5: return (void*)lb_collide_batch<Store, 256, false>;
+    default: return (void*)lb_collide_batch<Store, 128, true>;
+  }
+}
+
+void* lb_batch_kernel(int storage, int variant) {
+  switch (storage) {
+    case CACL_F16_SHIFTED: return lb_batch_fn<StoreF16>(variant);
+    case CACL_BF16_SHIFTED: return lb_batch_fn<StoreBF16>(variant);
+    default: return lb_batch_fn<StoreF32>(variant);
+  }
+}
+}  // namespace
+
+int lb_batch_occupancy(int storage, int variant) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lb_batch_kernel(storage, variant),
+                                                lb_batch_row(variant), 0);
+  return nb;
+}
+
+cudaError_t launch_lb_batch(const CaseDesc* cases, WorkList wl, int storage,
+                            int variant, int grid, int fc, int pc, cudaStream_t st) {
+  void* fn = lb_batch_kernel(storage, variant);
+  void* args[] = {(void*)&cases, (void*)&wl, (void*)&fc, (void*)&pc};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(lb_batch_row(variant)), args, 0, st);
 }
 
 }  // namespace cacl

@@ -92,13 +92,14 @@ __device__ __forceinline__ float muscl_axis(float vm2, float vm1, float v0,
 // One block: TX x TY output nodes per plane, TX x TY/2 threads; each thread
 // owns two vertically adjacent output nodes (rows 2 ty and 2 ty + 1), which
 // share most of their stencil reads and all per-thread bookkeeping.
-template <int TY, int ZC, int MINB>
-__global__ void __launch_bounds__(TX * TY / 2, MINB)
-phase_update_march(const float* __restrict__ phi, const float* __restrict__ afld,
-                   float* __restrict__ phi_out, const float* __restrict__ u,
-                   const uint8_t* __restrict__ flags,
-                   double* __restrict__ partials, int nblocks, Grid g,
-                   Consts k) {
+// One tile (bxi, byi, bzi) of one grid; its partial sums go to slot pb of
+// partials (phi* sums) and nblocks + pb (chi sums).
+template <int TY, int ZC>
+__device__ __forceinline__ void phase_tile_body(
+    int bxi, int byi, int bzi, int pb, const float* __restrict__ phi,
+    const float* __restrict__ afld, float* __restrict__ phi_out,
+    const float* __restrict__ u, const uint8_t* __restrict__ flags,
+    double* __restrict__ partials, int nblocks, const Grid& g, const Consts& k) {
   constexpr int PX = TX + 4, PY = TY + 4, NP = PX * PY;  // phi plane, halo 2
   constexpr int AX = TX + 2, AY = TY + 2, NA = AX * AY;  // a plane, halo 1
   constexpr int THREADS = TX * TY / 2;
@@ -114,7 +115,7 @@ phase_update_march(const float* __restrict__ phi, const float* __restrict__ afld
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = tx + TX * ty;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * ZC;
+  const int x0 = bxi * TX, y0 = byi * TY, z0 = bzi * ZC;
   const int zend = min(z0 + ZC, g.nz);
   const int nxy = g.nx * g.ny;
   const int64_t N = g.N;
@@ -372,9 +373,41 @@ phase_update_march(const float* __restrict__ phi, const float* __restrict__ afld
       m += (double)red[0][i].hi + (double)red[0][i].lo;
       w += (double)red[1][i].hi + (double)red[1][i].lo;
     }
-    const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    partials[b] = m;
-    partials[nblocks + b] = w;
+    partials[pb] = m;
+    partials[nblocks + pb] = w;
+  }
+}
+
+template <int TY, int ZC, int MINB>
+__global__ void __launch_bounds__(TX * TY / 2, MINB)
+phase_update_march(const float* __restrict__ phi, const float* __restrict__ afld,
+                   float* __restrict__ phi_out, const float* __restrict__ u,
+                   const uint8_t* __restrict__ flags,
+                   double* __restrict__ partials, int nblocks, Grid g,
+                   Consts k) {
+  const int pb = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  phase_tile_body<TY, ZC>(blockIdx.x, blockIdx.y, blockIdx.z, pb, phi, afld,
+                          phi_out, u, flags, partials, nblocks, g, k);
+}
+
+// Batched phi update: virtual block b is tile (bx, by, bz) of its case.
+template <int TY, int ZC, int MINB>
+__global__ void __launch_bounds__(TX * TY / 2, MINB)
+phase_update_batch(const CaseDesc* __restrict__ cases, WorkList wl, int pc) {
+  __shared__ CaseCursor cur;
+  if (threadIdx.x == 0 && threadIdx.y == 0) cur.begin();
+  __syncthreads();
+  int b0, b1;
+  block_range(wl, b0, b1);
+  for (int b = b0; b < b1; ++b) {
+    cur.seek(cases, wl, b);
+    const CaseDesc& cd = cur.d;
+    const int local = b - cur.cstart;
+    const int nbx = (cd.g.nx + TX - 1) / TX, nby = (cd.g.ny + TY - 1) / TY;
+    __syncthreads();  // the previous tile's shared-memory reads are done
+    phase_tile_body<TY, ZC>(local % nbx, (local / nbx) % nby, local / (nbx * nby),
+                            local, cd.phi[pc], cd.a, cd.phi[1 - pc], cd.u,
+                            cd.flags, cd.partials, cd.phase_nb, cd.g, cd.k);
   }
 }
 
@@ -435,6 +468,39 @@ int phase_blocks(const cacl_ctx* c) {
 }
 
 cudaError_t phase_init_attributes() { return cudaSuccess; }
+
+void phase_tile(int variant, int& ty, int& zc) {
+  const PhaseShape s = phase_shape(variant);
+  ty = s.ty;
+  zc = s.zc;
+}
+
+namespace {
+void* phase_batch_kernel(int variant) {
+  switch (variant) {
+    case 1: return (void*)phase_update_batch<8, 16, 4>;
+    case 2: return (void*)phase_update_batch<8, 32, 4>;
+    case 3: return (void*)phase_update_batch<16, 32, 2>;
+    default: return (void*)phase_update_batch<16, 16, 2>;
+  }
+}
+}  // namespace
+
+int phase_batch_occupancy(int variant) {
+  int nb = 0;
+  const PhaseShape s = phase_shape(variant);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, phase_batch_kernel(variant),
+                                                TX * s.ty / 2, 0);
+  return nb;
+}
+
+cudaError_t launch_phase_batch(const CaseDesc* cases, WorkList wl, int variant,
+                               int grid, int pc, cudaStream_t st) {
+  const PhaseShape s = phase_shape(variant);
+  void* args[] = {(void*)&cases, (void*)&wl, (void*)&pc};
+  return cudaLaunchKernel(phase_batch_kernel(variant), dim3(grid),
+                          dim3(TX, s.ty / 2, 1), args, 0, st);
+}
 
 cudaError_t launch_compressive(cacl_ctx* c, const float* phi) {
   const Grid g = c->g;

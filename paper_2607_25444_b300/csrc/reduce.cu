@@ -58,6 +58,23 @@ finalize_mass_ref(const double* __restrict__ partials, int nb,
   }
 }
 
+// Batched finalize: block c reduces case c's partials.
+__global__ void __launch_bounds__(FIN_THREADS)
+finalize_mass_batch(const CaseDesc* __restrict__ cases) {
+  __shared__ double sh[FIN_THREADS];
+  const CaseDesc& cd = cases[blockIdx.x];
+  const double m = block_sum(cd.partials, cd.phase_nb, sh);
+  const double w = block_sum(cd.partials + cd.phase_nb, cd.phase_nb, sh);
+  if (threadIdx.x == 0) {
+    MassScalars* ms = cd.mass;
+    const double lam = (w > 0.0) ? (ms->m_ref - m) / w : 0.0;
+    ms->m_star = m;
+    ms->w_sum = w;
+    ms->lambda = lam;
+    ms->lambda_f = (float)lam;
+  }
+}
+
 // phi = phi* + lambda chi(phi*) at fluid nodes, four nodes per thread.
 __global__ void __launch_bounds__(ELEM_THREADS)
 correct_phi(float* __restrict__ phi, const uint8_t* __restrict__ flags,
@@ -81,6 +98,34 @@ correct_phi(float* __restrict__ phi, const uint8_t* __restrict__ flags,
       const float s = phi[n];
       const float chi = (s > eps && s < 1.0f - eps) ? s * (1.0f - s) : 0.0f;
       if (!(flags[n] & FLAG_SOLID)) phi[n] = fmaf(lam, chi, s);
+    }
+  }
+}
+
+// Batched correction: virtual block b covers 4 * ELEM_THREADS nodes of its
+// case.
+__global__ void __launch_bounds__(ELEM_THREADS)
+correct_phi_batch(const CaseDesc* __restrict__ cases, WorkList wl, int pc) {
+  __shared__ CaseCursor cur;
+  if (threadIdx.x == 0) cur.begin();
+  __syncthreads();
+  int b0, b1;
+  block_range(wl, b0, b1);
+  for (int b = b0; b < b1; ++b) {
+    cur.seek(cases, wl, b);
+    const CaseDesc& cd = cur.d;
+    const float lam = cd.mass->lambda_f;
+    const float eps = cd.k.eps_phi;
+    float* phi = cd.phi[1 - pc];
+    const int64_t base = (int64_t)(b - cur.cstart) * 4 * ELEM_THREADS;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t n = base + j * ELEM_THREADS + threadIdx.x;
+      if (n < cd.g.N && !(cd.flags[n] & FLAG_SOLID)) {
+        const float s = phi[n];
+        const float chi = (s > eps && s < 1.0f - eps) ? s * (1.0f - s) : 0.0f;
+        phi[n] = fmaf(lam, chi, s);
+      }
     }
   }
 }
@@ -190,6 +235,15 @@ cudaError_t launch_correct(cacl_ctx* c, float* phi) {
   const int nb = (int)((N + 4 * ELEM_THREADS - 1) / (4 * ELEM_THREADS));
   correct_phi<<<nb, ELEM_THREADS, 0, c->stream>>>(phi, c->flags, c->mass, N,
                                                  c->k.eps_phi);
+  return cudaGetLastError();
+}
+
+int correct_batch_nodes() { return 4 * ELEM_THREADS; }
+
+cudaError_t launch_correct_batch(const CaseDesc* cases, int ncases, WorkList wl,
+                                 int grid, int pc, cudaStream_t st) {
+  finalize_mass_batch<<<ncases, FIN_THREADS, 0, st>>>(cases);
+  correct_phi_batch<<<grid, ELEM_THREADS, 0, st>>>(cases, wl, pc);
   return cudaGetLastError();
 }
 
