@@ -121,6 +121,14 @@ cacl_status cacl_set_geometry(cacl_ctx* ctx, const uint8_t* solid);
  * sign(cos theta_c) 1e6 when |sin theta_c| < 1e-6). */
 cacl_status cacl_set_contact_angle(cacl_ctx* ctx, const float* theta_deg);
 
+/* Contact angle per wall node, in wall-list order (host, W floats,
+ * degrees); the parameters of the adjoint's dL/dtheta. */
+cacl_status cacl_set_wall_angles(cacl_ctx* ctx, const float* theta_deg_wall);
+
+/* Change the surface tension (beta = 12 sigma/delta, kappa_phi = 3 sigma
+ * delta / 2, Eq. Fcap); the parameter of the adjoint's dL/dsigma. */
+cacl_status cacl_set_sigma(cacl_ctx* ctx, double sigma);
+
 /* Initial state from host arrays: phi (N floats, every node; values at
  * solid nodes seed the ghosts) and u (3N floats, component-major, or NULL
  * for rest). Populations become f^eq(p* = 0, u) (Eq. feq3); the mass
@@ -170,6 +178,26 @@ cacl_status cacl_get_mass(cacl_ctx* ctx, double* m_ref, double* m_star,
 
 /* Returns CACL_ERR_DIVERGED if phi or u holds a NaN or Inf. Synchronises. */
 cacl_status cacl_check_finite(cacl_ctx* ctx);
+
+/*
+ * Adjoint (reverse mode, hand-written) of nsteps full steps with respect to
+ * the contact angle of every wall node and the surface tension, for a loss
+ * L(phi) of the final phase field (FP32 populations only).
+ *   cacl_adjoint_forward advances the state by nsteps steps from the current
+ *   state, storing a checkpoint (f*, phi) every ckpt_every steps;
+ *   cacl_adjoint_backward takes dL/dphi of the final field (device, N
+ *   floats), recomputes each segment from its checkpoint with a per-step
+ *   tape, applies the transposed step in reverse (volume correction, phi
+ *   update, collide-stream, ghost map) and writes dL/dtheta_deg per wall node
+ *   (device, W doubles, wall-list order) and dL/dsigma (device, 1 double),
+ *   both accumulated in FP64. The state after the call is the one the
+ *   forward reached. At points where the step is not differentiable (minmod
+ *   switches, upwind choice, band edges of chi) the derivative of the branch
+ *   the forward took is used.
+ */
+cacl_status cacl_adjoint_forward(cacl_ctx* ctx, int nsteps, int ckpt_every);
+cacl_status cacl_adjoint_backward(cacl_ctx* ctx, const float* dL_dphi,
+                                  double* dL_dtheta, double* dL_dsigma);
 
 /*
  * Batches: many cases of uneven grid size advanced together (each stage of

@@ -30,7 +30,8 @@ EXPORTS = (
     "cacl_set_option", "cacl_get_info", "cacl_volume_correct_noalloc",
     "cacl_batch_create", "cacl_batch_destroy", "cacl_batch_last_error",
     "cacl_batch_case", "cacl_batch_step", "cacl_batch_set_option",
-    "cacl_batch_autotune",
+    "cacl_batch_autotune", "cacl_set_wall_angles", "cacl_set_sigma",
+    "cacl_adjoint_forward", "cacl_adjoint_backward",
 )
 OPT_PHASE_TILE = 1
 
@@ -105,6 +106,10 @@ def load():
     L.cacl_batch_set_option.argtypes = [vp, C.c_int, C.c_int]
     L.cacl_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int),
                                       C.POINTER(C.c_int), C.POINTER(C.c_float)]
+    L.cacl_set_wall_angles.argtypes = [vp, vp]
+    L.cacl_set_sigma.argtypes = [vp, C.c_double]
+    L.cacl_adjoint_forward.argtypes = [vp, C.c_int, C.c_int]
+    L.cacl_adjoint_backward.argtypes = [vp, vp, vp, vp]
     for name in EXPORTS:
         f = getattr(L, name)
         if name not in ("cacl_destroy", "cacl_last_error", "cacl_batch_destroy",
@@ -308,6 +313,23 @@ class Solver:
 
     def check_finite(self):
         self._check(self.L.cacl_check_finite(self.h))
+
+    def set_wall_angles(self, theta_deg_wall):
+        t = _f32(theta_deg_wall)
+        self._check(self.L.cacl_set_wall_angles(self.h, _ptr(t)))
+
+    def set_sigma(self, sigma):
+        self._check(self.L.cacl_set_sigma(self.h, float(sigma)))
+
+    def adjoint_forward(self, nsteps, ckpt_every):
+        self._check(self.L.cacl_adjoint_forward(self.h, int(nsteps), int(ckpt_every)))
+
+    def adjoint_backward(self, dl_dphi, dl_dtheta, dl_dsigma):
+        """Device torch tensors: dl_dphi (float32, N), dl_dtheta (float64,
+        W), dl_dsigma (float64, 1)."""
+        self._check(self.L.cacl_adjoint_backward(
+            self.h, C.c_void_p(dl_dphi.data_ptr()), C.c_void_p(dl_dtheta.data_ptr()),
+            C.c_void_p(dl_dsigma.data_ptr())))
 
     def set_option(self, option, value):
         self._check(self.L.cacl_set_option(self.h, int(option), int(value)))

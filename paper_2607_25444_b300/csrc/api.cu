@@ -183,6 +183,7 @@ void cacl_destroy(cacl_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graphs(c);
+  adjoint_free(c->adj);
   void* bufs[] = {c->f[0], c->f[1], c->phi[0], c->phi[1], c->u, c->a, c->flags,
                   c->w_idx, c->w_donor, c->w_q, c->w_n6, c->w_nw, c->w_cot,
                   c->w_theta, c->w_g, c->partials, c->mass, c->scan_scratch,
@@ -225,6 +226,30 @@ cacl_status cacl_set_geometry(cacl_ctx* c, const uint8_t* solid) {
   c->has_fields = false;
   c->geom_version++;
   return upload_angles(c, nullptr);
+}
+
+cacl_status cacl_set_wall_angles(cacl_ctx* c, const float* theta_w) {
+  if (!c || !theta_w) return fail(c, CACL_ERR_ARG, "null argument");
+  if (!c->has_geometry) return fail(c, CACL_ERR_STATE, "set_geometry first");
+  const int W = c->wall_count;
+  if (W == 0) return CACL_OK;
+  std::vector<float> ct(W);
+  for (int w = 0; w < W; ++w) ct[w] = (float)cot_internal(theta_w[w]);
+  CK(cudaMemcpyAsync(c->w_theta, theta_w, sizeof(float) * W,
+                     cudaMemcpyHostToDevice, c->stream), "upload theta");
+  CK(cudaMemcpyAsync(c->w_cot, ct.data(), sizeof(float) * W,
+                     cudaMemcpyHostToDevice, c->stream), "upload cot");
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  return CACL_OK;
+}
+
+cacl_status cacl_set_sigma(cacl_ctx* c, double sigma) {
+  if (!c || !(sigma >= 0)) return fail(c, CACL_ERR_ARG, "invalid surface tension");
+  c->p.sigma = sigma;
+  c->k.beta4 = (float)(4.0 * 12.0 * sigma / c->p.width);
+  c->k.kappa_phi = (float)(1.5 * sigma * c->p.width);
+  drop_graphs(c);  // the constants are launch arguments inside the graphs
+  return CACL_OK;
 }
 
 cacl_status cacl_set_contact_angle(cacl_ctx* c, const float* theta) {

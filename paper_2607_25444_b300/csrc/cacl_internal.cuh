@@ -227,6 +227,8 @@ __device__ __forceinline__ void block_range(const WorkList& wl, int& b0,
 
 }  // namespace cacl
 
+struct AdjointState;
+
 struct cacl_ctx {
   cacl_params p;
   cacl::Grid g;
@@ -273,6 +275,7 @@ struct cacl_ctx {
   // one-step graphs, indexed by (fcur, pcur)
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   int* bad_flag = nullptr;  // device word for cacl_check_finite
+  AdjointState* adj = nullptr;  // checkpoints, tape and adjoint fields
   int64_t device_bytes = 0;
 };
 
@@ -294,6 +297,7 @@ cudaError_t launch_from_storage(cacl_ctx* c, const void* src, float* dst);
 cudaError_t launch_check_finite(cacl_ctx* c, const float* phi, int* bad_dev);
 int phase_blocks(const cacl_ctx* c);
 int mass_ref_blocks(int64_t N);
+void adjoint_free(AdjointState* s);
 
 // Batched stages: one grid-strided launch runs the stage for every case of
 // a work-list; fc / pc select each case's current population / phi buffer.

@@ -1,0 +1,122 @@
+"""The hand-written adjoint of the CUDA step: dL/dtheta (per wall node) and
+dL/dsigma against central finite differences of the FP64 oracle, for a
+linear loss of the final phase field, on small grids."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2607_25444_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+NX, NY, NZ = 16, 16, 12
+STEPS, EVERY = 20, 6
+
+
+def _case(rho_g=0.5):
+    p = I.base_params(NX, NY, NZ, sigma=0.01, rho_l=1.0, rho_g=rho_g,
+                      nu_l=0.05, nu_g=0.1, theta_deg=80.0,
+                      gravity=(0.0, 0.0, -1e-5))
+    solid = I.walls_z(NX, NY, NZ)
+    phi = I.droplet(NX, NY, NZ, (8.0, 8.0, 0.5), 5.0, p["width"])
+    # contact angle in 2 x 2 patches on each wall
+    z, y, x = np.meshgrid(np.arange(NZ), np.arange(NY), np.arange(NX),
+                          indexing="ij")
+    patch = (x >= NX // 2).astype(int) + 2 * (y >= NY // 2).astype(int)
+    theta = np.array([55.0, 75.0, 105.0, 125.0])[patch].astype(np.float32)
+    r = I.fast_uniform((NZ, NY, NX), seed=31, lo=-1.0, hi=1.0)
+    r[solid == 1] = 0.0
+    return p, solid, phi, theta, patch, r
+
+
+def _oracle_loss(p, solid, phi, theta, r, sigma=None):
+    q = dict(p) if sigma is None else dict(p, sigma=sigma)
+    o = O.Oracle(q)
+    o.set_geometry(solid)
+    o.set_contact_angle(theta.astype(np.float64))
+    o.set_fields(phi.astype(np.float64))
+    o.step(STEPS)
+    return float((o.fields()[0] * r).sum())
+
+
+@pytest.fixture(scope="module")
+def gpu_grad():
+    import torch
+
+    from paper_2607_25444_b300 import cacl
+    p, solid, phi, theta, patch, r = _case()
+    s = cacl.Solver(p)
+    s.set_geometry(solid)
+    wl = s.wall_list()
+    s.set_fields(phi)
+    s.set_wall_angles(theta.reshape(-1)[wl["idx"]])
+    s.adjoint_forward(STEPS, EVERY)
+    phi_end = s.fields()[0]
+    W = wl["idx"].size
+    dth = torch.zeros(W, dtype=torch.float64, device="cuda")
+    dsg = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g = torch.from_numpy(r.reshape(-1).astype(np.float32)).cuda()
+    s.adjoint_backward(g, dth, dsg)
+    torch.cuda.synchronize()
+    # the plain step reaches the same final field
+    s2 = cacl.Solver(p)
+    s2.set_geometry(solid)
+    s2.set_fields(phi)
+    s2.set_wall_angles(theta.reshape(-1)[wl["idx"]])
+    s2.step(STEPS)
+    assert np.array_equal(s2.fields()[0], phi_end)
+    return dict(idx=wl["idx"], dtheta=dth.cpu().numpy(), dsigma=float(dsg.item()),
+                phi=phi_end)
+
+
+def test_forward_matches_oracle(gpu_grad):
+    p, solid, phi, theta, patch, r = _case()
+    o = O.Oracle(p)
+    o.set_geometry(solid)
+    o.set_contact_angle(theta.astype(np.float64))
+    o.set_fields(phi.astype(np.float64))
+    o.step(STEPS)
+    ref = o.fields()[0]
+    assert np.abs(gpu_grad["phi"] - ref).max() / np.abs(ref).max() < 1e-4
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_dtheta_directional_vs_oracle_fd(gpu_grad, seed):
+    p, solid, phi, theta, patch, r = _case()
+    g = I.SplitMix64(seed)
+    e_patch = np.array([g.uniform(-1.0, 1.0) for _ in range(4)])
+    e = e_patch[patch]
+    h = 0.01  # degrees
+    fd = (_oracle_loss(p, solid, phi, theta + h * e, r) -
+          _oracle_loss(p, solid, phi, theta - h * e, r)) / (2 * h)
+    ad = float((gpu_grad["dtheta"] * e.reshape(-1)[gpu_grad["idx"]]).sum())
+    print(f"dtheta direction {seed}: adjoint {ad:.9e} fd {fd:.9e} "
+          f"rel {abs(ad - fd) / abs(fd):.2e}")
+    assert abs(ad - fd) <= 1e-3 * abs(fd), (ad, fd)
+
+
+def test_dsigma_vs_oracle_fd(gpu_grad):
+    p, solid, phi, theta, patch, r = _case()
+    h = 1e-6
+    fd = (_oracle_loss(p, solid, phi, theta, r, p["sigma"] + h) -
+          _oracle_loss(p, solid, phi, theta, r, p["sigma"] - h)) / (2 * h)
+    ad = gpu_grad["dsigma"]
+    print(f"dsigma: adjoint {ad:.9e} fd {fd:.9e} rel {abs(ad - fd) / abs(fd):.2e}")
+    assert abs(ad - fd) <= 1e-3 * abs(fd), (ad, fd)
+
+
+def test_autograd_function_matches_direct_call(gpu_grad):
+    import torch
+
+    from paper_2607_25444_b300 import adjoint, cacl
+    p, solid, phi, theta, patch, r = _case()
+    s = cacl.Solver(p)
+    s.set_geometry(solid)
+    idx = s.wall_list()["idx"]
+    th = torch.tensor(theta.reshape(-1)[idx], dtype=torch.float64, requires_grad=True)
+    sg = torch.tensor(p["sigma"], dtype=torch.float64, requires_grad=True)
+    out = adjoint.rollout(th, sg, s, phi, None, STEPS, EVERY)
+    loss = (out * torch.from_numpy(r.astype(np.float32)).cuda()).sum()
+    loss.backward()
+    assert np.allclose(th.grad.cpu().numpy(), gpu_grad["dtheta"], rtol=1e-6, atol=1e-12)
+    assert abs(sg.grad.item() - gpu_grad["dsigma"]) <= 1e-6 * abs(gpu_grad["dsigma"])
