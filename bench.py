@@ -300,6 +300,55 @@ def run_batched(args, torch, cacl, stream):
             "finite": finite}
 
 
+def run_adjoint(args, torch, cacl, stream):
+    """Adjoint/forward cost on a wettability-inference case shaped like the
+    workload of the adjoint: 96^3, flat walls, theta in 8 x 8 patches drawn
+    from [45, 135] deg (seeded), droplet R = 16, sigma = 0.01, nu = 0.1."""
+    from paper_2607_25444_b300 import inputs as I
+    n = 96
+    p = I.base_params(n, n, n, sigma=0.01, nu_l=0.1, nu_g=0.1, theta_deg=90.0)
+    solid = I.walls_z(n, n, n)
+    phi = I.droplet(n, n, n, (n / 2, n / 2, 0.5), 16.0, p["width"])
+    s = cacl.Solver(p)
+    s.set_geometry(solid)
+    idx = s.wall_list()["idx"]
+    x, y = idx % n, (idx // n) % n
+    patches = I.SplitMix64(7).array(64, 45.0, 135.0)
+    theta_w = patches[(y // 12) * 8 + (x // 12)].astype(np.float32)
+    steps, every = 200, 50
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    s.set_fields(phi)
+    s.set_wall_angles(theta_w)
+    s.step(10)  # warm-up
+    s.set_fields(phi)
+    ev[0].record(stream)
+    s.step(steps)
+    ev[1].record(stream)
+    s.set_fields(phi)
+    ev[2].record(stream)
+    s.adjoint_forward(steps, every)
+    ev[3].record(stream)
+    g = torch.zeros(n * n * n, dtype=torch.float32, device="cuda")
+    g.view(n, n, n)[1] = 1.0  # dL/dphi of the footprint layer sum
+    dth = torch.zeros(idx.size, dtype=torch.float64, device="cuda")
+    dsg = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ev[4].record(stream)
+    s.adjoint_backward(g, dth, dsg)
+    ev[5].record(stream)
+    torch.cuda.synchronize()
+    t_plain = ev[0].elapsed_time(ev[1])
+    t_fwd = ev[2].elapsed_time(ev[3])
+    t_bwd = ev[4].elapsed_time(ev[5])
+    s.close()
+    return {"workload": "96^3 flat walls, theta in 8x8 patches U[45,135] deg, R=16",
+            "steps": steps, "ckpt_every": every,
+            "forward_ms_per_step": t_plain / steps,
+            "checkpointed_forward_ms_per_step": t_fwd / steps,
+            "backward_ms_per_step": t_bwd / steps,
+            "backward_over_forward": t_bwd / t_plain,
+            "note": "backward includes the recompute of every segment with its tape"}
+
+
 def run_cuda(args):
     import torch
     rank, world, local = dist_env()
@@ -409,6 +458,9 @@ def run_cuda(args):
     batched = None
     if not args.no_batch and world == 1:
         batched = run_batched(args, torch, cacl, stream)
+    adj = None
+    if not args.no_adjoint and world == 1:
+        adj = run_adjoint(args, torch, cacl, stream)
 
     if rank != 0:
         return
@@ -451,6 +503,7 @@ def run_cuda(args):
         "cpu_baseline": cpu,
         "mixed": mixed or None,
         "batched": batched,
+        "adjoint": adj,
     }
     print(json.dumps(line), flush=True)
 
@@ -466,6 +519,8 @@ def main():
                          "for profiling captures)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="population storage of the headline line")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint/forward cost measurement")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched impact-sweep timing")
     ap.add_argument("--no-variants", action="store_true",
