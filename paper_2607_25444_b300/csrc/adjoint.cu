@@ -667,6 +667,7 @@ struct AdjointState {
   int W = 0;
   // checkpoints: f* (27N floats) and phi (N) at steps 0, every, 2 every, ...
   std::vector<float*> ck_f, ck_phi;
+  MassScalars* ck_mass = nullptr;  // mass record (incl. rounding key) per checkpoint
   // per-step tape of one segment
   std::vector<float*> t_fprev, t_phipre, t_phig, t_u, t_a, t_phis;
   MassScalars* t_mass = nullptr;  // [every]
@@ -686,7 +687,7 @@ void adjoint_free(AdjointState* s) {
   for (auto* v : {&s->ck_f, &s->ck_phi, &s->t_fprev, &s->t_phipre, &s->t_phig,
                   &s->t_u, &s->t_a, &s->t_phis})
     for (float* p : *v) cudaFree(p);
-  void* bufs[] = {s->t_mass, s->fb, s->fb2, s->phib, s->phisb, s->phigb, s->ub,
+  void* bufs[] = {s->ck_mass, s->t_mass, s->fb, s->fb2, s->phib, s->phisb, s->phigb, s->ub,
                   s->ab, s->face, s->finb, s->nodeb, s->wd, s->thetab, s->sigmab,
                   s->partial, s->row_start, s->row_entry};
   for (void* b : bufs)
@@ -828,6 +829,7 @@ cacl_status cacl_adjoint_forward(cacl_ctx* c, int nsteps, int every) {
       }
     }
     ACK(alloc(&s->t_mass, every), "alloc tape");
+    ACK(alloc(&s->ck_mass, nck), "alloc checkpoint");
     ACK(alloc(&s->fb, (size_t)Q * N), "alloc adjoint");
     ACK(alloc(&s->fb2, (size_t)Q * N), "alloc adjoint");
     ACK(alloc(&s->finb, (size_t)Q * N), "alloc adjoint");
@@ -853,6 +855,8 @@ cacl_status cacl_adjoint_forward(cacl_ctx* c, int nsteps, int every) {
       ACK(cudaMemcpyAsync(s->ck_f[ck], c->f[c->fcur], sizeof(float) * Q * N,
                           cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
       ACK(cudaMemcpyAsync(s->ck_phi[ck], c->phi[c->pcur], sizeof(float) * N,
+                          cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
+      ACK(cudaMemcpyAsync(s->ck_mass + ck, c->mass, sizeof(MassScalars),
                           cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
     }
     const cacl_status st = cacl_step(c, 1);
@@ -885,6 +889,10 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
   ACK(cudaMemcpyAsync(save_phi, c->phi[c->pcur], sizeof(float) * N,
                       cudaMemcpyDeviceToDevice, st), "save");
   const int save_fc = c->fcur, save_pc = c->pcur;
+  MassScalars save_mass;
+  ACK(cudaMemcpyAsync(&save_mass, c->mass, sizeof(MassScalars), cudaMemcpyDeviceToHost,
+                      st), "save");
+  ACK(cudaStreamSynchronize(st), "sync");
 
   ACK(cudaMemcpyAsync(s->phib, dL_dphi, sizeof(float) * N, cudaMemcpyDeviceToDevice, st),
       "seed");
@@ -900,6 +908,8 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
     ACK(cudaMemcpyAsync(c->f[c->fcur], s->ck_f[seg], sizeof(float) * Q * N,
                         cudaMemcpyDeviceToDevice, st), "restore");
     ACK(cudaMemcpyAsync(c->phi[c->pcur], s->ck_phi[seg], sizeof(float) * N,
+                        cudaMemcpyDeviceToDevice, st), "restore");
+    ACK(cudaMemcpyAsync(c->mass, s->ck_mass + seg, sizeof(MassScalars),
                         cudaMemcpyDeviceToDevice, st), "restore");
     for (int t = 0; t < len; ++t) {
       const cacl_status r = taped_step(c, s, t);
@@ -950,6 +960,8 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
                       cudaMemcpyDeviceToDevice, st), "restore");
   ACK(cudaMemcpyAsync(c->phi[c->pcur], save_phi, sizeof(float) * N,
                       cudaMemcpyDeviceToDevice, st), "restore");
+  ACK(cudaMemcpyAsync(c->mass, &save_mass, sizeof(MassScalars), cudaMemcpyHostToDevice,
+                      st), "restore");
   ACK(cudaStreamSynchronize(st), "sync");
   cudaFree(save_f);
   cudaFree(save_phi);

@@ -146,8 +146,30 @@ struct MassScalars {
   double w_sum;
   double lambda;
   float lambda_f;
-  int pad;
+  uint32_t step;  // corrections applied since set_fields (rounding key)
 };
+
+// phi + d rounded to FP32 without bias: the exact residual of the sum
+// (Knuth's two-sum) decides, against a uniform number drawn from a
+// counter-based hash of (step, node), whether to move one unit in the last
+// place towards it, so the expected stored value is phi + d. A correction
+// far below the resolution of phi is then applied on average instead of
+// being rounded away every step.
+__device__ __forceinline__ float add_unbiased(float s, float d, uint32_t step,
+                                              uint64_t node) {
+  const float t = s + d;
+  const float bb = t - s;
+  const float e = (s - (t - bb)) + (d - bb);
+  if (e == 0.f) return t;
+  // splitmix64 finalizer of the key
+  uint64_t z = ((uint64_t)step << 40) ^ node ^ 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  const float u = (float)(z >> 40) * (1.0f / 16777216.0f);
+  const float nb = nextafterf(t, e > 0.f ? INFINITY : -INFINITY);
+  return (u * fabsf(nb - t) < fabsf(e)) ? nb : t;
+}
 
 // One case of a batch as the batched kernels see it: grid, constants and
 // the device buffers of the case's own context.

@@ -41,6 +41,7 @@ finalize_mass(const double* __restrict__ partials, int nb, MassScalars* ms) {
     ms->w_sum = w;
     ms->lambda = lam;
     ms->lambda_f = (float)lam;
+    ms->step += 1;
   }
 }
 
@@ -55,6 +56,7 @@ finalize_mass_ref(const double* __restrict__ partials, int nb,
     ms->w_sum = 0.0;
     ms->lambda = 0.0;
     ms->lambda_f = 0.0f;
+    ms->step = 0;
   }
 }
 
@@ -72,14 +74,17 @@ finalize_mass_batch(const CaseDesc* __restrict__ cases) {
     ms->w_sum = w;
     ms->lambda = lam;
     ms->lambda_f = (float)lam;
+    ms->step += 1;
   }
 }
 
-// phi = phi* + lambda chi(phi*) at fluid nodes, four nodes per thread.
+// phi = phi* + lambda chi(phi*) at fluid nodes, four nodes per thread,
+// rounded without bias.
 __global__ void __launch_bounds__(ELEM_THREADS)
 correct_phi(float* __restrict__ phi, const uint8_t* __restrict__ flags,
             const MassScalars* __restrict__ ms, int64_t N, float eps) {
   const float lam = ms->lambda_f;
+  const uint32_t step = ms->step;
   const int64_t i4 = ((int64_t)blockIdx.x * ELEM_THREADS + threadIdx.x) * 4;
   if (i4 + 3 < N) {
     float4 v = *reinterpret_cast<const float4*>(phi + i4);
@@ -90,14 +95,14 @@ correct_phi(float* __restrict__ phi, const uint8_t* __restrict__ flags,
     for (int j = 0; j < 4; ++j) {
       const float s = pv[j];
       const float chi = (s > eps && s < 1.0f - eps) ? s * (1.0f - s) : 0.0f;
-      if (!(fa[j] & FLAG_SOLID)) pv[j] = fmaf(lam, chi, s);
+      if (!(fa[j] & FLAG_SOLID)) pv[j] = add_unbiased(s, lam * chi, step, i4 + j);
     }
     *reinterpret_cast<float4*>(phi + i4) = v;
   } else {
     for (int64_t n = i4; n < N; ++n) {
       const float s = phi[n];
       const float chi = (s > eps && s < 1.0f - eps) ? s * (1.0f - s) : 0.0f;
-      if (!(flags[n] & FLAG_SOLID)) phi[n] = fmaf(lam, chi, s);
+      if (!(flags[n] & FLAG_SOLID)) phi[n] = add_unbiased(s, lam * chi, step, n);
     }
   }
 }
@@ -115,6 +120,7 @@ correct_phi_batch(const CaseDesc* __restrict__ cases, WorkList wl, int pc) {
     cur.seek(cases, wl, b);
     const CaseDesc& cd = cur.d;
     const float lam = cd.mass->lambda_f;
+    const uint32_t step = cd.mass->step;
     const float eps = cd.k.eps_phi;
     float* phi = cd.phi[1 - pc];
     const int64_t base = (int64_t)(b - cur.cstart) * 4 * ELEM_THREADS;
@@ -124,7 +130,7 @@ correct_phi_batch(const CaseDesc* __restrict__ cases, WorkList wl, int pc) {
       if (n < cd.g.N && !(cd.flags[n] & FLAG_SOLID)) {
         const float s = phi[n];
         const float chi = (s > eps && s < 1.0f - eps) ? s * (1.0f - s) : 0.0f;
-        phi[n] = fmaf(lam, chi, s);
+        phi[n] = add_unbiased(s, lam * chi, step, n);
       }
     }
   }
