@@ -241,8 +241,13 @@ cacl_status cacl_batch_autotune(cacl_batch* batch, int steps, int* lb_variant,
 /* Launch-shape options (results do not depend on them beyond rounding
  * order). CACL_OPT_PHASE_TILE selects the tile of the phase update:
  * 0 = 32x16 nodes x 16 planes, 1 = 32x8 x 16, 2 = 32x8 x 32,
- * 3 = 32x16 x 32. Returns CACL_ERR_ARG for an unknown option or value. */
-typedef enum { CACL_OPT_PHASE_TILE = 1 } cacl_option;
+ * 3 = 32x16 x 32. CACL_OPT_PHASE_PIPE selects how the phase update stages
+ * its planes in shared memory: 0 = automatic (asynchronous 16-byte copies
+ * when nx is a multiple of 4 and the fields are 16-byte aligned, else
+ * staging through registers), 1 = registers, 2 = asynchronous copies
+ * (CACL_ERR_ARG when nx is not a multiple of 4). Both give bit-identical
+ * results. Returns CACL_ERR_ARG for an unknown option or value. */
+typedef enum { CACL_OPT_PHASE_TILE = 1, CACL_OPT_PHASE_PIPE = 2 } cacl_option;
 cacl_status cacl_set_option(cacl_ctx* ctx, int option, int value);
 
 /* Grid size N and bytes of device memory the context holds. */

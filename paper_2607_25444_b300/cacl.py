@@ -34,6 +34,7 @@ EXPORTS = (
     "cacl_adjoint_forward", "cacl_adjoint_backward",
 )
 OPT_PHASE_TILE = 1
+OPT_PHASE_PIPE = 2  # 0 auto, 1 register staging, 2 asynchronous copies
 
 
 class CaclError(RuntimeError):

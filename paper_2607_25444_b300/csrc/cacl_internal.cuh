@@ -285,6 +285,7 @@ struct cacl_ctx {
 
   // kernel shape choices (cacl_set_option)
   int phase_variant = 0;
+  int phase_pipe = 0;      // 0 auto, 1 register staging, 2 cp.async staging
   int phase_nblocks = 0;   // blocks of the last phase-update launch
 
   // reductions

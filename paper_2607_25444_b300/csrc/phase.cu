@@ -89,11 +89,190 @@ __device__ __forceinline__ float muscl_axis(float vm2, float vm1, float v0,
   return (solp ? 0.f : fp) - (solm ? 0.f : fm);
 }
 
+// Registers a thread carries up its pair of columns (output rows a and b)
+// from plane to plane: phi at kz-2..kz+2, solid flags at kz-1..kz+1, the
+// in-plane partial stencils of planes kz-1..kz+1
+//   H = Dd_x S_y a_x + S_x Dd_y a_y, V = S_x S_y a_z, L = S_x S_y phi,
+// the z velocity at kz-1..kz+1, and the two partial sums.
+struct March {
+  float ca5[5], cb5[5];
+  bool sa3[3], sb3[3];
+  float Ha[3], Hb[3], Va[3], Vb[3], La[3], Lb[3];
+  float uza[3], uzb[3];
+  DF msum, wsum;
+};
+
+__device__ __forceinline__ void march_init(March& m) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) m.ca5[i] = m.cb5[i] = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    m.sa3[i] = m.sb3[i] = false;
+    m.Ha[i] = m.Hb[i] = m.Va[i] = m.Vb[i] = m.La[i] = m.Lb[i] = 0.f;
+    m.uza[i] = m.uzb[i] = 0.f;
+  }
+  m.msum = {0.f, 0.f};
+  m.wsum = {0.f, 0.f};
+}
+
+// Advance the carried registers by one plane: the in-plane partials of plane
+// kz + 1 (phi plane P1 with row pitch PP, a planes with row pitch AP; cp and
+// ca index row a of the thread), the own columns' phi at kz + 2 (P2) and
+// solid flags at kz + 1 (S1).
+template <int PP, int AP>
+__device__ __forceinline__ void march_roll(March& m, const float* P1,
+                                           const float* P2, const uint8_t* S1,
+                                           const float* axp, const float* ayp,
+                                           const float* azp, int cp, int ca) {
+  float xm_[4], xp_[4], ym_[4][3], zz[4][3], pp[4][3];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {  // a-plane rows y-1 .. y+2 of the pair
+    const int o = ca + (r - 1) * AP;
+    xm_[r] = axp[o - 1];
+    xp_[r] = axp[o + 1];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      ym_[r][d] = ayp[o + d - 1];
+      zz[r][d] = azp[o + d - 1];
+      pp[r][d] = P1[cp + (r - 1) * PP + d - 1];
+    }
+  }
+  float H2[2], V2[2], L2[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {  // output row j uses rows j .. j+2
+    const float sxp = xp_[j] + fmaf(4.f, xp_[j + 1], xp_[j + 2]);
+    const float sxm = xm_[j] + fmaf(4.f, xm_[j + 1], xm_[j + 2]);
+    const float d0 = ym_[j + 2][0] - ym_[j][0];
+    const float d1 = ym_[j + 2][1] - ym_[j][1];
+    const float d2 = ym_[j + 2][2] - ym_[j][2];
+    H2[j] = (sxp - sxm + d0 + fmaf(4.f, d1, d2)) * (1.0f / 36.0f);
+    float rz[3], rl[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      rz[r] = zz[j + r][0] + fmaf(4.f, zz[j + r][1], zz[j + r][2]);
+      rl[r] = pp[j + r][0] + fmaf(4.f, pp[j + r][1], pp[j + r][2]);
+    }
+    V2[j] = (rz[0] + fmaf(4.f, rz[1], rz[2])) * (1.0f / 36.0f);
+    L2[j] = (rl[0] + fmaf(4.f, rl[1], rl[2])) * (1.0f / 36.0f);
+  }
+  m.Ha[0] = m.Ha[1]; m.Ha[1] = m.Ha[2]; m.Ha[2] = H2[0];
+  m.Hb[0] = m.Hb[1]; m.Hb[1] = m.Hb[2]; m.Hb[2] = H2[1];
+  m.Va[0] = m.Va[1]; m.Va[1] = m.Va[2]; m.Va[2] = V2[0];
+  m.Vb[0] = m.Vb[1]; m.Vb[1] = m.Vb[2]; m.Vb[2] = V2[1];
+  m.La[0] = m.La[1]; m.La[1] = m.La[2]; m.La[2] = L2[0];
+  m.Lb[0] = m.Lb[1]; m.Lb[1] = m.Lb[2]; m.Lb[2] = L2[1];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    m.ca5[i] = m.ca5[i + 1];
+    m.cb5[i] = m.cb5[i + 1];
+  }
+  m.ca5[4] = P2[cp];
+  m.cb5[4] = P2[cp + PP];
+  m.sa3[0] = m.sa3[1]; m.sa3[1] = m.sa3[2]; m.sa3[2] = (S1[cp] & FLAG_SOLID) != 0;
+  m.sb3[0] = m.sb3[1]; m.sb3[1] = m.sb3[2]; m.sb3[2] = (S1[cp + PP] & FLAG_SOLID) != 0;
+}
+
+// One output node: Eq. phi_update_muscl with the isotropic diffusion and the
+// compressive term, written to *out, and its contribution to the partial
+// sums (Eqs. tentative_phase_field_mass, mass_correction_normalization).
+// c indexes the node in P0 / S0; v0 and c* are phi along z (kz-2..kz+2),
+// yv* phi along y, sz* / sy* the solid flags of the z and y neighbours,
+// u* the cell velocities at -1, 0, +1 along each axis, h* / vv* / l* the
+// in-plane partials of planes kz-1..kz+1.
+__device__ __forceinline__ void march_node(
+    DF& msum, DF& wsum, const float* P0, const uint8_t* S0, int c, float v0,
+    float cm2, float cm1, float cp1, float cp2, bool solc, bool szm, bool szp,
+    float yv0, float yv1, float yv3, float yv4, bool sym, bool syp, float ux0,
+    float ux1, float ux2, float uy0, float uy1, float uy2, float uz0, float uz1,
+    float uz2, float h0, float h1, float h2, float vv0, float vv2, float l0,
+    float l1, float l2, float* out, const Consts& k) {
+  if (solc) {
+    *out = v0;
+    return;
+  }
+  float div = muscl_axis(P0[c - 2], P0[c - 1], v0, P0[c + 1], P0[c + 2],
+                         (S0[c - 1] & FLAG_SOLID) != 0,
+                         (S0[c + 1] & FLAG_SOLID) != 0, ux0, ux1, ux2);
+  div += muscl_axis(yv0, yv1, v0, yv3, yv4, sym, syp, uy0, uy1, uy2);
+  div += muscl_axis(cm2, cm1, v0, cp1, cp2, szm, szp, uz0, uz1, uz2);
+  // lap = 6 (S_z L - phi), div_iso a = 3 S_z H + 3 Dd_z V
+  const float lap = l0 + fmaf(4.f, l1, l2) - 6.f * v0;
+  const float diva = 0.5f * (h0 + fmaf(4.f, h1, h2) + vv2 - vv0);
+  const float vs = v0 - div + k.mobility * lap - k.kappa * diva;
+  *out = vs;
+  df_add(msum, vs);
+  const float chi = (vs > k.eps_phi && vs < 1.0f - k.eps_phi) ? vs * (1.0f - vs) : 0.f;
+  df_add(wsum, chi);
+}
+
+// Both output nodes of the pair at plane kz: P0 / S0 hold phi and the flags
+// of plane kz (row pitch PP), ux* / uy4 the in-plane velocities (x
+// component at x-1, x, x+1 of rows a and b; y component at rows ya-1, ya,
+// yb, yb+1), outa / outb the destinations.
+template <int PP>
+__device__ __forceinline__ void march_emit(March& m, const float* P0,
+                                           const uint8_t* S0, int cp,
+                                           const float (&uxa)[3],
+                                           const float (&uxb)[3],
+                                           const float (&uy4)[4], bool act_a,
+                                           bool act_b, float* outa, float* outb,
+                                           const Consts& k) {
+  // phi along y at rows ya-2 .. yb+2 of the own column
+  const float py0 = P0[cp - 2 * PP], py1 = P0[cp - PP], py4 = P0[cp + 2 * PP],
+              py5 = P0[cp + 3 * PP];
+  const bool sy0 = (S0[cp - PP] & FLAG_SOLID) != 0;
+  const bool sy3 = (S0[cp + 2 * PP] & FLAG_SOLID) != 0;
+  if (act_a)
+    march_node(m.msum, m.wsum, P0, S0, cp, m.ca5[2], m.ca5[0], m.ca5[1], m.ca5[3],
+               m.ca5[4], m.sa3[1], m.sa3[0], m.sa3[2], py0, py1, m.cb5[2], py4,
+               sy0, m.sb3[1], uxa[0], uxa[1], uxa[2], uy4[0], uy4[1], uy4[2],
+               m.uza[0], m.uza[1], m.uza[2], m.Ha[0], m.Ha[1], m.Ha[2], m.Va[0],
+               m.Va[2], m.La[0], m.La[1], m.La[2], outa, k);
+  if (act_b)
+    march_node(m.msum, m.wsum, P0, S0, cp + PP, m.cb5[2], m.cb5[0], m.cb5[1],
+               m.cb5[3], m.cb5[4], m.sb3[1], m.sb3[0], m.sb3[2], py1, m.ca5[2],
+               py4, py5, m.sa3[1], sy3, uxb[0], uxb[1], uxb[2], uy4[1], uy4[2],
+               uy4[3], m.uzb[0], m.uzb[1], m.uzb[2], m.Hb[0], m.Hb[1], m.Hb[2],
+               m.Vb[0], m.Vb[2], m.Lb[0], m.Lb[1], m.Lb[2], outb, k);
+}
+
+// Block reduction of the two partial sums; thread 0 writes them as FP64 to
+// slot pb of partials (phi* sums) and nblocks + pb (chi sums).
+template <int THREADS>
+__device__ __forceinline__ void block_partials(DF msum, DF wsum, int tid,
+                                               double* __restrict__ partials,
+                                               int pb, int nblocks) {
+  __shared__ DF red[2][THREADS / 32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    msum = df_merge(msum, df_shfl_down(msum, off));
+    wsum = df_merge(wsum, df_shfl_down(wsum, off));
+  }
+  const int lane = tid & 31, warp = tid >> 5;
+  if (lane == 0) {
+    red[0][warp] = msum;
+    red[1][warp] = wsum;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double mm = 0.0, ww = 0.0;
+    for (int i = 0; i < THREADS / 32; ++i) {
+      mm += (double)red[0][i].hi + (double)red[0][i].lo;
+      ww += (double)red[1][i].hi + (double)red[1][i].lo;
+    }
+    partials[pb] = mm;
+    partials[nblocks + pb] = ww;
+  }
+}
+
 // One block: TX x TY output nodes per plane, TX x TY/2 threads; each thread
 // owns two vertically adjacent output nodes (rows 2 ty and 2 ty + 1), which
 // share most of their stencil reads and all per-thread bookkeeping.
 // One tile (bxi, byi, bzi) of one grid; its partial sums go to slot pb of
 // partials (phi* sums) and nblocks + pb (chi sums).
+// Staging through registers: each thread loads its share of the next planes
+// one plane ahead and stores it to shared memory at the next step. Works for
+// any grid size.
 template <int TY, int ZC>
 __device__ __forceinline__ void phase_tile_body(
     int bxi, int byi, int bzi, int pb, const float* __restrict__ phi,
@@ -111,7 +290,6 @@ __device__ __forceinline__ void phase_tile_body(
   __shared__ float s_phi[4][NP];
   __shared__ uint8_t s_sol[4][NP];
   __shared__ float s_a[2][3][NA];
-  __shared__ DF red[2][THREADS / 32];
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = tx + TX * ty;
@@ -201,27 +379,44 @@ __device__ __forceinline__ void phase_tile_body(
   fetch_phi(zf);  // plane z0, stored at the first step
   fetch_a(za);    // plane z0 - 1
   __syncthreads();
-  // own columns: phi at kz-2..kz+2, solid at kz-1..kz+1, rows a and b
-  float ca5[5] = {0.f, 0.f, 0.f, s_phi[(z0 - 2) & 3][cp], s_phi[(z0 - 1) & 3][cp]};
-  float cb5[5] = {0.f, 0.f, 0.f, s_phi[(z0 - 2) & 3][cp + PX], s_phi[(z0 - 1) & 3][cp + PX]};
-  bool sa3[3] = {false, false, s_sol[(z0 - 2) & 3][cp] != 0};
-  bool sb3[3] = {false, false, s_sol[(z0 - 2) & 3][cp + PX] != 0};
-  float Ha[3] = {0.f, 0.f, 0.f}, Hb[3] = {0.f, 0.f, 0.f};
-  float Va[3] = {0.f, 0.f, 0.f}, Vb[3] = {0.f, 0.f, 0.f};
-  float La[3] = {0.f, 0.f, 0.f}, Lb[3] = {0.f, 0.f, 0.f};
-  // z velocity of the own columns at kz-1, kz, kz+1 (rolled)
+  March m;
+  march_init(m);
+  m.ca5[3] = s_phi[(z0 - 2) & 3][cp];
+  m.ca5[4] = s_phi[(z0 - 1) & 3][cp];
+  m.cb5[3] = s_phi[(z0 - 2) & 3][cp + PX];
+  m.cb5[4] = s_phi[(z0 - 1) & 3][cp + PX];
+  // z velocity of the own columns: rolled, with the next plane's in nza/nzb
   const float* uz_ = u + 2 * N;
-  float uza[3], uzb[3];
+  float nza, nzb;
   {
     const int64_t zm = (int64_t)mod(z0 - 1, g.nz) * nxy;
     const int64_t zc = (int64_t)mod(z0, g.nz) * nxy;
-    uza[0] = 0.f; uzb[0] = 0.f;
-    uza[1] = __ldg(uz_ + zm + own_a);
-    uzb[1] = __ldg(uz_ + zm + own_b);
-    uza[2] = __ldg(uz_ + zc + own_a);
-    uzb[2] = __ldg(uz_ + zc + own_b);
+    const int64_t zn = (int64_t)mod(z0 + 1, g.nz) * nxy;
+    m.uza[1] = __ldg(uz_ + zm + own_a);
+    m.uzb[1] = __ldg(uz_ + zm + own_b);
+    m.uza[2] = __ldg(uz_ + zc + own_a);
+    m.uzb[2] = __ldg(uz_ + zc + own_b);
+    nza = __ldg(uz_ + zn + own_a);
+    nzb = __ldg(uz_ + zn + own_b);
   }
-  DF msum = {0.f, 0.f}, wsum = {0.f, 0.f};
+  // x and y velocities of the next output plane
+  float nxa[3] = {0.f, 0.f, 0.f}, nxb[3] = {0.f, 0.f, 0.f};
+  float ny4[4] = {0.f, 0.f, 0.f, 0.f};
+  auto fetch_u = [&](int kz) {
+    const float* ux_ = u + (int64_t)kz * nxy;
+    const float* uy_ = ux_ + N;
+    const int ra = g.nx * min(ya, g.ny - 1), rb = g.nx * ybw;
+    nxa[0] = __ldg(ux_ + ra + xm);
+    nxa[1] = __ldg(ux_ + own_a);
+    nxa[2] = __ldg(ux_ + ra + xp);
+    nxb[0] = __ldg(ux_ + rb + xm);
+    nxb[1] = __ldg(ux_ + own_b);
+    nxb[2] = __ldg(ux_ + rb + xp);
+    ny4[0] = __ldg(uy_ + g.nx * yam + xc);
+    ny4[1] = __ldg(uy_ + own_a);
+    ny4[2] = __ldg(uy_ + own_b);
+    ny4[3] = __ldg(uy_ + g.nx * ybp + xc);
+  };
 
   for (int kz = z0 - 2; kz < zend; ++kz) {
     store_phi(kz + 2);
@@ -233,149 +428,212 @@ __device__ __forceinline__ void phase_tile_body(
       fetch_a(zfa);
     }
     const bool out = kz >= z0;
-    // velocities of the output plane: x and y components, and the z
-    // component one plane ahead for the rolled column values
+    // velocities of the output plane, fetched one plane ahead: x and y
+    // components of plane kz (loaded at kz - 1), and the z component rolled
+    // along the own columns
     float uxa[3], uxb[3], uy4[4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      uxa[i] = nxa[i];
+      uxb[i] = nxb[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) uy4[i] = ny4[i];
     if (out) {
-      const float* ux_ = u + (int64_t)kz * nxy;
-      const float* uy_ = ux_ + N;
-      const int zp = (kz == g.nz - 1) ? -(g.nz - 1) * nxy : nxy;
-      const int ra = g.nx * min(ya, g.ny - 1), rb = g.nx * ybw;
-      uxa[0] = __ldg(ux_ + ra + xm);
-      uxa[1] = __ldg(ux_ + own_a);
-      uxa[2] = __ldg(ux_ + ra + xp);
-      uxb[0] = __ldg(ux_ + rb + xm);
-      uxb[1] = __ldg(ux_ + own_b);
-      uxb[2] = __ldg(ux_ + rb + xp);
-      uy4[0] = __ldg(uy_ + g.nx * yam + xc);
-      uy4[1] = __ldg(uy_ + own_a);
-      uy4[2] = __ldg(uy_ + own_b);
-      uy4[3] = __ldg(uy_ + g.nx * ybp + xc);
-      const float* uzk = uz_ + (int64_t)kz * nxy + zp;
-      uza[0] = uza[1]; uza[1] = uza[2]; uza[2] = __ldg(uzk + own_a);
-      uzb[0] = uzb[1]; uzb[1] = uzb[2]; uzb[2] = __ldg(uzk + own_b);
+      m.uza[0] = m.uza[1]; m.uza[1] = m.uza[2]; m.uza[2] = nza;
+      m.uzb[0] = m.uzb[1]; m.uzb[1] = m.uzb[2]; m.uzb[2] = nzb;
+      const int z2 = (kz + 2 >= g.nz) ? kz + 2 - g.nz : kz + 2;
+      nza = __ldg(uz_ + (int64_t)z2 * nxy + own_a);
+      nzb = __ldg(uz_ + (int64_t)z2 * nxy + own_b);
     }
+    if (kz + 1 >= z0 && kz + 1 < zend) fetch_u(kz + 1);
     __syncthreads();
-    const float* P0 = s_phi[kz & 3];
-    const float* P1 = s_phi[(kz + 1) & 3];
-    // in-plane parts for plane kz + 1 at rows a and b:
-    //   H = Dd_x S_y a_x + S_x Dd_y a_y, V = S_x S_y a_z, L = S_x S_y phi
-    {
-      const float* axp = s_a[(kz + 1) & 1][0];
-      const float* ayp = s_a[(kz + 1) & 1][1];
-      const float* azp = s_a[(kz + 1) & 1][2];
-      float xm_[4], xp_[4], ym_[4][3], zz[4][3], pp[4][3];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {  // a-plane rows 2ty .. 2ty+3 (y-1 .. y+2)
-        const int o = ca + (r - 1) * AX;
-        xm_[r] = axp[o - 1];
-        xp_[r] = axp[o + 1];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          ym_[r][d] = ayp[o + d - 1];
-          zz[r][d] = azp[o + d - 1];
-          pp[r][d] = P1[cp + (r - 1) * PX + d - 1];
-        }
-      }
-      float H2[2], V2[2], L2[2];
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {  // output row j uses rows j .. j+2
-        const float sxp = xp_[j] + fmaf(4.f, xp_[j + 1], xp_[j + 2]);
-        const float sxm = xm_[j] + fmaf(4.f, xm_[j + 1], xm_[j + 2]);
-        const float d0 = ym_[j + 2][0] - ym_[j][0];
-        const float d1 = ym_[j + 2][1] - ym_[j][1];
-        const float d2 = ym_[j + 2][2] - ym_[j][2];
-        H2[j] = (sxp - sxm + d0 + fmaf(4.f, d1, d2)) * (1.0f / 36.0f);
-        float rz[3], rl[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          rz[r] = zz[j + r][0] + fmaf(4.f, zz[j + r][1], zz[j + r][2]);
-          rl[r] = pp[j + r][0] + fmaf(4.f, pp[j + r][1], pp[j + r][2]);
-        }
-        V2[j] = (rz[0] + fmaf(4.f, rz[1], rz[2])) * (1.0f / 36.0f);
-        L2[j] = (rl[0] + fmaf(4.f, rl[1], rl[2])) * (1.0f / 36.0f);
-      }
-      Ha[0] = Ha[1]; Ha[1] = Ha[2]; Ha[2] = H2[0];
-      Hb[0] = Hb[1]; Hb[1] = Hb[2]; Hb[2] = H2[1];
-      Va[0] = Va[1]; Va[1] = Va[2]; Va[2] = V2[0];
-      Vb[0] = Vb[1]; Vb[1] = Vb[2]; Vb[2] = V2[1];
-      La[0] = La[1]; La[1] = La[2]; La[2] = L2[0];
-      Lb[0] = Lb[1]; Lb[1] = Lb[2]; Lb[2] = L2[1];
-      const float* P2 = s_phi[(kz + 2) & 3];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        ca5[i] = ca5[i + 1];
-        cb5[i] = cb5[i + 1];
-      }
-      ca5[4] = P2[cp];
-      cb5[4] = P2[cp + PX];
-      sa3[0] = sa3[1]; sa3[1] = sa3[2]; sa3[2] = s_sol[(kz + 1) & 3][cp] != 0;
-      sb3[0] = sb3[1]; sb3[1] = sb3[2]; sb3[2] = s_sol[(kz + 1) & 3][cp + PX] != 0;
-    }
+    march_roll<PX, AX>(m, s_phi[(kz + 1) & 3], s_phi[(kz + 2) & 3],
+                       s_sol[(kz + 1) & 3], s_a[(kz + 1) & 1][0],
+                       s_a[(kz + 1) & 1][1], s_a[(kz + 1) & 1][2], cp, ca);
     if (!out) continue;
-    // output plane kz, rows a and b
-    const uint8_t* sc = s_sol[kz & 3];
-    // phi along y at rows ya-2 .. yb+2 of the own column
-    const float py0 = P0[cp - 2 * PX], py1 = P0[cp - PX], py4 = P0[cp + 2 * PX],
-                py5 = P0[cp + 3 * PX];
-    const bool sy0 = sc[cp - PX] != 0, sy3 = sc[cp + 2 * PX] != 0;
-    auto emit = [&](bool act, int own, int c, float v0, float cm2, float cm1,
-                    float cp1, float cp2, bool solc, bool szm, bool szp,
-                    float yv0, float yv1, float yv3, float yv4, bool sym, bool syp,
-                    float ux0, float ux1, float ux2, float uy0, float uy1,
-                    float uy2, float uz0, float uz1, float uz2, float h0,
-                    float h1, float h2, float vv0, float vv2, float l0, float l1,
-                    float l2) {
-      if (!act) return;
-      const int64_t n = own + (int64_t)kz * nxy;
-      if (solc) {
-        phi_out[n] = v0;
-        return;
-      }
-      float div = muscl_axis(P0[c - 2], P0[c - 1], v0, P0[c + 1], P0[c + 2],
-                             sc[c - 1] != 0, sc[c + 1] != 0, ux0, ux1, ux2);
-      div += muscl_axis(yv0, yv1, v0, yv3, yv4, sym, syp, uy0, uy1, uy2);
-      div += muscl_axis(cm2, cm1, v0, cp1, cp2, szm, szp, uz0, uz1, uz2);
-      // lap = 6 (S_z L - phi), div_iso a = 3 S_z H + 3 Dd_z V
-      const float lap = l0 + fmaf(4.f, l1, l2) - 6.f * v0;
-      const float diva = 0.5f * (h0 + fmaf(4.f, h1, h2) + vv2 - vv0);
-      const float vs = v0 - div + k.mobility * lap - k.kappa * diva;
-      phi_out[n] = vs;
-      df_add(msum, vs);
-      const float chi = (vs > k.eps_phi && vs < 1.0f - k.eps_phi) ? vs * (1.0f - vs) : 0.f;
-      df_add(wsum, chi);
-    };
-    emit(act_a, own_a, cp, ca5[2], ca5[0], ca5[1], ca5[3], ca5[4], sa3[1], sa3[0],
-         sa3[2], py0, py1, cb5[2], py4, sy0, sb3[1], uxa[0], uxa[1], uxa[2],
-         uy4[0], uy4[1], uy4[2], uza[0], uza[1], uza[2], Ha[0], Ha[1], Ha[2],
-         Va[0], Va[2], La[0], La[1], La[2]);
-    emit(act_b, own_b, cp + PX, cb5[2], cb5[0], cb5[1], cb5[3], cb5[4], sb3[1],
-         sb3[0], sb3[2], py1, ca5[2], py4, py5, sa3[1], sy3, uxb[0], uxb[1],
-         uxb[2], uy4[1], uy4[2], uy4[3], uzb[0], uzb[1], uzb[2], Hb[0], Hb[1],
-         Hb[2], Vb[0], Vb[2], Lb[0], Lb[1], Lb[2]);
+    float* po = phi_out + (int64_t)kz * nxy;
+    march_emit<PX>(m, s_phi[kz & 3], s_sol[kz & 3], cp, uxa, uxb, uy4, act_a,
+                   act_b, po + own_a, po + own_b, k);
+  }
+  block_partials<THREADS>(m.msum, m.wsum, tid, partials, pb, nblocks);
+}
+
+// cp.async copies global -> shared (16 bytes through L2 only, 4 bytes through
+// L1), and their commit / wait.
+__device__ __forceinline__ void cp_async16(void* s, const void* gsrc) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(s);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* s, const void* gsrc) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(s);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Shared-memory layout of the copy-staged tile. Every plane window spans
+// x0-4 .. x0+35 (CW = 40 columns, ten 16-byte chunks) so that each chunk is
+// 16-byte aligned in global memory when nx is a multiple of 4. Per bundle of
+// copies: phi and the flags of plane t+2 (rows y0-2 .. y0+TY+1), a of plane
+// t+1 (rows y0-1 .. y0+TY), u_x of plane t (rows y0 .. y0+TY-1, all 40
+// columns), u_y of plane t (rows y0-1 .. y0+TY, columns x0 .. x0+31) and u_z
+// of plane t+1 (rows y0 .. y0+TY-1, columns x0 .. x0+31). Bundles are issued
+// D planes ahead into rings of RP (phi, flags) and RA (a, u) slots.
+constexpr int CW = TX + 8;
+constexpr int NCH = CW / 4;
+
+template <int TY, int D>
+struct CopyTile {
+  static constexpr int PR = TY + 4, AR = TY + 2;
+  static constexpr int RP = 4 + D, RA = 2 + D;
+  static constexpr int PHI = PR * CW;               // floats per phi slot
+  static constexpr int AC = AR * CW;                // floats per a component
+  static constexpr int UX = TY * CW, UY = (TY + 2) * TX, UZ = TY * TX;
+  static constexpr int ASLOT = 3 * AC + UX + UY + UZ;  // a and u of one plane
+  static constexpr int FLG = PR * CW;               // bytes per flags slot
+  static constexpr size_t bytes =
+      sizeof(float) * ((size_t)RP * PHI + (size_t)RA * ASLOT) + (size_t)RP * FLG;
+};
+
+// The same tile as phase_tile_body with every plane staged by cp.async
+// copies issued D planes ahead (no register staging, no shared-memory
+// stores by the threads). Requires nx % 4 == 0. smem is the dynamic shared
+// memory of CopyTile<TY, D>::bytes.
+template <int TY, int ZC, int D>
+__device__ __forceinline__ void phase_tile_copy(
+    int bxi, int byi, int bzi, int pb, const float* __restrict__ phi,
+    const float* __restrict__ afld, float* __restrict__ phi_out,
+    const float* __restrict__ u, const uint8_t* __restrict__ flags,
+    double* __restrict__ partials, int nblocks, const Grid& g, const Consts& k,
+    float* smem) {
+  using L = CopyTile<TY, D>;
+  constexpr int THREADS = TX * TY / 2;
+  static_assert(L::PR * NCH <= THREADS && L::AR * NCH <= THREADS &&
+                    L::UY / 4 <= THREADS,
+                "one copy job of each kind per thread");
+  float* s_phi = smem;                                  // [RP][PHI]
+  float* s_au = smem + L::RP * L::PHI;                  // [RA][ASLOT]
+  uint8_t* s_flg = (uint8_t*)(s_au + L::RA * L::ASLOT); // [RP][FLG]
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = tx + TX * ty;
+  const int x0 = bxi * TX, y0 = byi * TY, z0 = bzi * ZC;
+  const int zend = min(z0 + ZC, g.nz);
+  const int nxy = g.nx * g.ny;
+  const int64_t N = g.N;
+
+  // this thread's copy jobs: plane offsets (global) and slot offsets (shared)
+  const bool hp = tid < L::PR * NCH;  // phi + flags chunk
+  const bool ha = tid < L::AR * NCH;  // a chunk (3 components)
+  const bool hx = tid < TY * NCH;     // u_x chunk
+  const bool hy = tid < L::UY / 4;    // u_y chunk
+  const bool hz = tid < L::UZ / 4;    // u_z chunk
+  const int cx_ = tid % NCH, rx_ = tid / NCH;       // 40-column windows
+  const int c8 = tid % (TX / 4), r8 = tid / (TX / 4);  // 32-column windows
+  const int wx = mod(x0 - 4 + 4 * cx_, g.nx);
+  const int w8 = mod(x0 + 4 * c8, g.nx);
+  const int gp = wx + g.nx * mod(y0 - 2 + rx_, g.ny), sp = rx_ * CW + 4 * cx_;
+  const int ga = wx + g.nx * mod(y0 - 1 + rx_, g.ny);  // slot offset sp
+  const int gx = wx + g.nx * mod(y0 + rx_, g.ny);      // slot offset sp
+  const int gy = w8 + g.nx * mod(y0 - 1 + r8, g.ny), s8 = r8 * TX + 4 * c8;
+  const int gz = w8 + g.nx * mod(y0 + r8, g.ny);       // slot offset s8
+
+  const int nb = zend - z0 + 2;  // bundles / steps: planes z0-2 .. zend-1
+  auto issue_phi = [&](int p, int slot) {  // phi and flags of plane p
+    const int64_t zo = (int64_t)mod(p, g.nz) * nxy;
+    if (hp) {
+      cp_async16(s_phi + slot * L::PHI + sp, phi + zo + gp);
+      cp_async4(s_flg + slot * L::FLG + sp, flags + zo + gp);
+    }
+  };
+  auto issue = [&](int b) {  // bundle b: step kz = z0 - 2 + b
+    const int t = z0 - 2 + b;
+    issue_phi(t + 2, (b + 2) % L::RP);
+    float* sa = s_au + (b % L::RA) * L::ASLOT;
+    const int64_t z1 = (int64_t)mod(t + 1, g.nz) * nxy;
+    if (ha) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        cp_async16(sa + c * L::AC + sp, afld + c * N + z1 + ga);
+    }
+    if (hz) cp_async16(sa + 3 * L::AC + L::UX + L::UY + s8, u + 2 * N + z1 + gz);
+    if (b >= 2) {  // output plane t
+      const int64_t z0o = (int64_t)mod(t, g.nz) * nxy;
+      if (hx) cp_async16(sa + 3 * L::AC + sp, u + z0o + gx);
+      if (hy) cp_async16(sa + 3 * L::AC + L::UX + s8, u + N + z0o + gy);
+    }
+  };
+
+  // the two output rows of this thread
+  const int x = x0 + tx;
+  const int ya = y0 + 2 * ty, yb = ya + 1;
+  const bool act_a = (x < g.nx) && (ya < g.ny);
+  const bool act_b = (x < g.nx) && (yb < g.ny);
+  const int own_a = x + g.nx * ya;  // used only when active
+  const int own_b = own_a + g.nx;
+  const int cp = (tx + 4) + CW * (2 * ty + 2);  // row a in phi-window coords
+  const int ca = (tx + 4) + CW * (2 * ty + 1);  // row a in a-window coords
+  const int cxu = (tx + 4) + CW * (2 * ty);     // row a in the u_x window
+  const int cyu = tx + TX * (2 * ty + 1);       // row a in the u_y window
+  const int czu = tx + TX * (2 * ty);           // row a in the u_z window
+
+  // prologue: phi planes z0-2, z0-1 with bundle 0, then bundles 1 .. D-1
+  issue_phi(z0 - 2, 0);
+  issue_phi(z0 - 1, 1);
+  issue(0);
+  cp_async_commit();
+#pragma unroll
+  for (int b = 1; b < D; ++b) {
+    if (b < nb) issue(b);
+    cp_async_commit();
   }
 
-  // block reduction of the two partial sums
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    msum = df_merge(msum, df_shfl_down(msum, off));
-    wsum = df_merge(wsum, df_shfl_down(wsum, off));
-  }
-  const int lane = tid & 31, warp = tid >> 5;
-  if (lane == 0) {
-    red[0][warp] = msum;
-    red[1][warp] = wsum;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double m = 0.0, w = 0.0;
-    for (int i = 0; i < THREADS / 32; ++i) {
-      m += (double)red[0][i].hi + (double)red[0][i].lo;
-      w += (double)red[1][i].hi + (double)red[1][i].lo;
+  March m;
+  march_init(m);
+  for (int b = 0; b < nb; ++b) {
+    if (b + D < nb) issue(b + D);
+    cp_async_commit();
+    cp_async_wait<D>();
+    __syncthreads();
+    const float* P0 = s_phi + (b % L::RP) * L::PHI;
+    const float* P1 = s_phi + ((b + 1) % L::RP) * L::PHI;
+    const float* P2 = s_phi + ((b + 2) % L::RP) * L::PHI;
+    const uint8_t* S0 = s_flg + (b % L::RP) * L::FLG;
+    const uint8_t* S1 = s_flg + ((b + 1) % L::RP) * L::FLG;
+    const float* sa = s_au + (b % L::RA) * L::ASLOT;
+    const float* su = sa + 3 * L::AC;
+    if (b == 0) {  // own columns at planes z0-2, z0-1
+      m.ca5[3] = P0[cp];
+      m.cb5[3] = P0[cp + CW];
+      m.ca5[4] = P1[cp];
+      m.cb5[4] = P1[cp + CW];
     }
-    partials[pb] = m;
-    partials[nblocks + pb] = w;
+    const float* suz = su + L::UX + L::UY;
+    m.uza[0] = m.uza[1]; m.uza[1] = m.uza[2]; m.uza[2] = suz[czu];
+    m.uzb[0] = m.uzb[1]; m.uzb[1] = m.uzb[2]; m.uzb[2] = suz[czu + TX];
+    march_roll<CW, CW>(m, P1, P2, S1, sa, sa + L::AC, sa + 2 * L::AC, cp, ca);
+    if (b < 2) continue;
+    const float uxa[3] = {su[cxu - 1], su[cxu], su[cxu + 1]};
+    const float uxb[3] = {su[cxu + CW - 1], su[cxu + CW], su[cxu + CW + 1]};
+    const float* suy = su + L::UX;
+    const float uy4[4] = {suy[cyu - TX], suy[cyu], suy[cyu + TX], suy[cyu + 2 * TX]};
+    float* po = phi_out + (int64_t)(z0 - 2 + b) * nxy;
+    march_emit<CW>(m, P0, S0, cp, uxa, uxb, uy4, act_a, act_b, po + own_a,
+                   po + own_b, k);
   }
+  cp_async_wait_all();
+  block_partials<THREADS>(m.msum, m.wsum, tid, partials, pb, nblocks);
 }
 
 template <int TY, int ZC, int MINB>
@@ -388,6 +646,19 @@ phase_update_march(const float* __restrict__ phi, const float* __restrict__ afld
   const int pb = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   phase_tile_body<TY, ZC>(blockIdx.x, blockIdx.y, blockIdx.z, pb, phi, afld,
                           phi_out, u, flags, partials, nblocks, g, k);
+}
+
+template <int TY, int ZC, int D, int MINB>
+__global__ void __launch_bounds__(TX * TY / 2, MINB)
+phase_update_copy(const float* __restrict__ phi, const float* __restrict__ afld,
+                  float* __restrict__ phi_out, const float* __restrict__ u,
+                  const uint8_t* __restrict__ flags,
+                  double* __restrict__ partials, int nblocks, Grid g,
+                  Consts k) {
+  extern __shared__ __align__(16) float dsm[];
+  const int pb = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  phase_tile_copy<TY, ZC, D>(blockIdx.x, blockIdx.y, blockIdx.z, pb, phi, afld,
+                             phi_out, u, flags, partials, nblocks, g, k, dsm);
 }
 
 // Batched phi update: virtual block b is tile (bx, by, bz) of its case.
@@ -467,7 +738,40 @@ int phase_blocks(const cacl_ctx* c) {
   return nb;
 }
 
-cudaError_t phase_init_attributes() { return cudaSuccess; }
+namespace {
+// copy-staged kernels of the four tile shapes, with their shared memory
+constexpr int COPY_D = 2;  // planes of copies in flight ahead of the compute
+struct CopyKernel {
+  void* fn;
+  size_t smem;
+};
+CopyKernel copy_kernel(int variant) {
+  switch (variant) {
+    case 1: return {(void*)phase_update_copy<8, 16, COPY_D, 4>, CopyTile<8, COPY_D>::bytes};
+    case 2: return {(void*)phase_update_copy<8, 32, COPY_D, 4>, CopyTile<8, COPY_D>::bytes};
+    case 3: return {(void*)phase_update_copy<16, 32, COPY_D, 2>, CopyTile<16, COPY_D>::bytes};
+    default: return {(void*)phase_update_copy<16, 16, COPY_D, 2>, CopyTile<16, COPY_D>::bytes};
+  }
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+}  // namespace
+
+cudaError_t phase_init_attributes() {
+  for (int v = 0; v < 4; ++v) {
+    const CopyKernel ck = copy_kernel(v);
+    const cudaError_t e = cudaFuncSetAttribute(
+        ck.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ck.smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+bool phase_copy_ok(const Grid& g, const void* phi_in, const void* phi_out,
+                   const void* a, const void* u, const void* flags) {
+  return g.nx % 4 == 0 && aligned16(phi_in) && aligned16(phi_out) &&
+         aligned16(a) && aligned16(u) && ((uintptr_t)flags & 3u) == 0;
+}
 
 void phase_tile(int variant, int& ty, int& zc) {
   const PhaseShape s = phase_shape(variant);
@@ -516,6 +820,21 @@ cudaError_t launch_phase(cacl_ctx* c, const float* phi_in, float* phi_out) {
   c->phase_nblocks = nb;
   const PhaseShape s = phase_shape(v);
   const dim3 block(TX, s.ty / 2, 1);
+  const bool copy_ok = phase_copy_ok(c->g, phi_in, phi_out, c->a, c->u, c->flags);
+  if (c->phase_pipe == 2 && !copy_ok) return cudaErrorInvalidValue;
+  if (c->phase_pipe != 1 && copy_ok) {
+    const CopyKernel ck = copy_kernel(v);
+    const float* a = c->a;
+    const float* u = c->u;
+    const uint8_t* fl = c->flags;
+    double* part = c->partials;
+    Grid g = c->g;
+    Consts k = c->k;
+    int nbk = nb;
+    void* args[] = {(void*)&phi_in, (void*)&a, (void*)&phi_out, (void*)&u,
+                    (void*)&fl, (void*)&part, (void*)&nbk, (void*)&g, (void*)&k};
+    return cudaLaunchKernel(ck.fn, grid, block, args, ck.smem, c->stream);
+  }
   switch (v) {
     case 1:
       phase_update_march<8, 16, 4><<<grid, block, 0, c->stream>>>(
