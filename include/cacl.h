@@ -245,8 +245,9 @@ cacl_status cacl_batch_autotune(cacl_batch* batch, int steps, int* lb_variant,
  * its planes in shared memory: 0 = automatic (asynchronous 16-byte copies
  * when nx is a multiple of 4 and the fields are 16-byte aligned, else
  * staging through registers), 1 = registers, 2 = asynchronous copies
- * (CACL_ERR_ARG when nx is not a multiple of 4). Both give bit-identical
- * results. Returns CACL_ERR_ARG for an unknown option or value. */
+ * (CACL_ERR_ARG when nx is not a multiple of 4 or nz < 2). Both give
+ * bit-identical results. Returns CACL_ERR_ARG for an unknown option or
+ * value. */
 typedef enum { CACL_OPT_PHASE_TILE = 1, CACL_OPT_PHASE_PIPE = 2 } cacl_option;
 cacl_status cacl_set_option(cacl_ctx* ctx, int option, int value);
 

@@ -61,15 +61,31 @@ __device__ __forceinline__ DF df_shfl_down(DF v, int off) {
   return r;
 }
 
-// minmod(a, b) = 0 if a b <= 0, else sign(a) min(|a|, |b|) (Eq. minmod)
+// minmod(a, b) = 0 if a b <= 0, else sign(a) min(|a|, |b|) (Eq. minmod),
+// evaluated as max(min(a, b), min(max(a, b), 0)): for a, b > 0 it gives
+// min(a, b), for a, b < 0 max(a, b), and 0 for opposite signs or a zero.
 __device__ __forceinline__ float minmod(float a, float b) {
-  const float m = fminf(fabsf(a), fabsf(b));
-  return (a * b > 0.f) ? copysignf(m, a) : 0.f;
+  return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.f));
 }
 
 __device__ __forceinline__ int mod(int i, int n) {
   const int r = i % n;
   return r < 0 ? r + n : r;
+}
+
+// i wrapped into [0, n) for i in [-n, 2n)
+__device__ __forceinline__ int wrap1(int i, int n) {
+  return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// Upwind flux u_f phi_f through the face between cells l and r (Eqs.
+// face_flux_def, recon_lr_x, upwind_select_x): u_f = (u_l + u_r) / 2, and
+// phi_f the left state phi_l + s_l / 2 when u_f >= 0, else the right state
+// phi_r - s_r / 2 (s the minmod slopes).
+__device__ __forceinline__ float face_flux(float ul, float ur, float vl,
+                                           float sl, float vr, float sr) {
+  const float uf = 0.5f * (ul + ur);
+  return uf * ((uf >= 0.f) ? fmaf(0.5f, sl, vl) : fmaf(-0.5f, sr, vr));
 }
 
 // Net advective flux difference along one axis (Eqs. divF .. upwind_select):
@@ -82,43 +98,48 @@ __device__ __forceinline__ float muscl_axis(float vm2, float vm1, float v0,
   const float sm = minmod(vm1 - vm2, v0 - vm1);
   const float s0 = minmod(v0 - vm1, vp1 - v0);
   const float sp = minmod(vp1 - v0, vp2 - vp1);
-  const float ufp = 0.5f * (uc + up);
-  const float ufm = 0.5f * (um + uc);
-  const float fp = ufp * ((ufp >= 0.f) ? fmaf(0.5f, s0, v0) : fmaf(-0.5f, sp, vp1));
-  const float fm = ufm * ((ufm >= 0.f) ? fmaf(0.5f, sm, vm1) : fmaf(-0.5f, s0, v0));
+  const float fp = face_flux(uc, up, v0, s0, vp1, sp);
+  const float fm = face_flux(um, uc, vm1, sm, v0, s0);
   return (solp ? 0.f : fp) - (solm ? 0.f : fm);
 }
 
 // Registers a thread carries up its pair of columns (output rows a and b)
-// from plane to plane: phi at kz-2..kz+2, solid flags at kz-1..kz+1, the
-// in-plane partial stencils of planes kz-1..kz+1
+// from plane to plane, at output plane kz: phi at kz..kz+2, solid flags at
+// kz-1..kz+1, the z velocity at kz and kz+1, the z slope at kz+1 and the z
+// face fluxes at kz-1/2 and kz+1/2 (each face and slope is formed once, by
+// the plane below it, and is the same number the node-wise Eq. divF uses
+// from either side), the in-plane partial stencils of planes kz-1..kz+1
 //   H = Dd_x S_y a_x + S_x Dd_y a_y, V = S_x S_y a_z, L = S_x S_y phi,
-// the z velocity at kz-1..kz+1, and the two partial sums.
+// and the two partial sums.
 struct March {
-  float ca5[5], cb5[5];
+  float ca[3], cb[3];
   bool sa3[3], sb3[3];
   float Ha[3], Hb[3], Va[3], Vb[3], La[3], Lb[3];
-  float uza[3], uzb[3];
+  float uza[2], uzb[2];
+  float sza, szb;               // z slope at kz + 1
+  float fzma, fzmb, fzpa, fzpb;  // z fluxes at kz - 1/2 and kz + 1/2
   DF msum, wsum;
 };
 
 __device__ __forceinline__ void march_init(March& m) {
 #pragma unroll
-  for (int i = 0; i < 5; ++i) m.ca5[i] = m.cb5[i] = 0.f;
-#pragma unroll
   for (int i = 0; i < 3; ++i) {
+    m.ca[i] = m.cb[i] = 0.f;
     m.sa3[i] = m.sb3[i] = false;
     m.Ha[i] = m.Hb[i] = m.Va[i] = m.Vb[i] = m.La[i] = m.Lb[i] = 0.f;
-    m.uza[i] = m.uzb[i] = 0.f;
   }
+  m.uza[0] = m.uza[1] = m.uzb[0] = m.uzb[1] = 0.f;
+  m.sza = m.szb = 0.f;
+  m.fzma = m.fzmb = m.fzpa = m.fzpb = 0.f;
   m.msum = {0.f, 0.f};
   m.wsum = {0.f, 0.f};
 }
 
 // Advance the carried registers by one plane: the in-plane partials of plane
 // kz + 1 (phi plane P1 with row pitch PP, a planes with row pitch AP; cp and
-// ca index row a of the thread), the own columns' phi at kz + 2 (P2) and
-// solid flags at kz + 1 (S1).
+// ca index row a of the thread), the own columns' phi at kz + 2 (P2), solid
+// flags at kz + 1 (S1), then the z slope at kz + 1 and the z flux at
+// kz + 1/2 (m.uz* must hold u_z at kz and kz + 1).
 template <int PP, int AP>
 __device__ __forceinline__ void march_roll(March& m, const float* P1,
                                            const float* P2, const uint8_t* S1,
@@ -161,31 +182,32 @@ __device__ __forceinline__ void march_roll(March& m, const float* P1,
   m.Vb[0] = m.Vb[1]; m.Vb[1] = m.Vb[2]; m.Vb[2] = V2[1];
   m.La[0] = m.La[1]; m.La[1] = m.La[2]; m.La[2] = L2[0];
   m.Lb[0] = m.Lb[1]; m.Lb[1] = m.Lb[2]; m.Lb[2] = L2[1];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    m.ca5[i] = m.ca5[i + 1];
-    m.cb5[i] = m.cb5[i + 1];
-  }
-  m.ca5[4] = P2[cp];
-  m.cb5[4] = P2[cp + PP];
+  m.ca[0] = m.ca[1]; m.ca[1] = m.ca[2]; m.ca[2] = P2[cp];
+  m.cb[0] = m.cb[1]; m.cb[1] = m.cb[2]; m.cb[2] = P2[cp + PP];
   m.sa3[0] = m.sa3[1]; m.sa3[1] = m.sa3[2]; m.sa3[2] = (S1[cp] & FLAG_SOLID) != 0;
   m.sb3[0] = m.sb3[1]; m.sb3[1] = m.sb3[2]; m.sb3[2] = (S1[cp + PP] & FLAG_SOLID) != 0;
+  // z slope at kz + 1 and z flux at kz + 1/2, from the slope at kz
+  const float sa1 = minmod(m.ca[1] - m.ca[0], m.ca[2] - m.ca[1]);
+  const float sb1 = minmod(m.cb[1] - m.cb[0], m.cb[2] - m.cb[1]);
+  m.fzma = m.fzpa;
+  m.fzmb = m.fzpb;
+  m.fzpa = face_flux(m.uza[0], m.uza[1], m.ca[0], m.sza, m.ca[1], sa1);
+  m.fzpb = face_flux(m.uzb[0], m.uzb[1], m.cb[0], m.szb, m.cb[1], sb1);
+  m.sza = sa1;
+  m.szb = sb1;
 }
 
-// One output node: Eq. phi_update_muscl with the isotropic diffusion and the
-// compressive term, written to *out, and its contribution to the partial
-// sums (Eqs. tentative_phase_field_mass, mass_correction_normalization).
-// c indexes the node in P0 / S0; v0 and c* are phi along z (kz-2..kz+2),
-// yv* phi along y, sz* / sy* the solid flags of the z and y neighbours,
-// u* the cell velocities at -1, 0, +1 along each axis, h* / vv* / l* the
-// in-plane partials of planes kz-1..kz+1.
+// Rest of one output node: Eq. phi_update_muscl with the isotropic
+// diffusion and the compressive term, written to *out, and its contribution
+// to the partial sums (Eqs. tentative_phase_field_mass,
+// mass_correction_normalization). c indexes the node in P0 / S0; dy and dz
+// are the (masked) y and z flux differences, u* the x velocities at -1, 0,
+// +1, h* / vv* / l* the in-plane partials of planes kz-1..kz+1.
 __device__ __forceinline__ void march_node(
     DF& msum, DF& wsum, const float* P0, const uint8_t* S0, int c, float v0,
-    float cm2, float cm1, float cp1, float cp2, bool solc, bool szm, bool szp,
-    float yv0, float yv1, float yv3, float yv4, bool sym, bool syp, float ux0,
-    float ux1, float ux2, float uy0, float uy1, float uy2, float uz0, float uz1,
-    float uz2, float h0, float h1, float h2, float vv0, float vv2, float l0,
-    float l1, float l2, float* out, const Consts& k) {
+    bool solc, float dy, float dz, float ux0, float ux1, float ux2, float h0,
+    float h1, float h2, float vv0, float vv2, float l0, float l1, float l2,
+    float* out, const Consts& k) {
   if (solc) {
     *out = v0;
     return;
@@ -193,8 +215,8 @@ __device__ __forceinline__ void march_node(
   float div = muscl_axis(P0[c - 2], P0[c - 1], v0, P0[c + 1], P0[c + 2],
                          (S0[c - 1] & FLAG_SOLID) != 0,
                          (S0[c + 1] & FLAG_SOLID) != 0, ux0, ux1, ux2);
-  div += muscl_axis(yv0, yv1, v0, yv3, yv4, sym, syp, uy0, uy1, uy2);
-  div += muscl_axis(cm2, cm1, v0, cp1, cp2, szm, szp, uz0, uz1, uz2);
+  div += dy;
+  div += dz;
   // lap = 6 (S_z L - phi), div_iso a = 3 S_z H + 3 Dd_z V
   const float lap = l0 + fmaf(4.f, l1, l2) - 6.f * v0;
   const float diva = 0.5f * (h0 + fmaf(4.f, h1, h2) + vv2 - vv0);
@@ -208,7 +230,8 @@ __device__ __forceinline__ void march_node(
 // Both output nodes of the pair at plane kz: P0 / S0 hold phi and the flags
 // of plane kz (row pitch PP), ux* / uy4 the in-plane velocities (x
 // component at x-1, x, x+1 of rows a and b; y component at rows ya-1, ya,
-// yb, yb+1), outa / outb the destinations.
+// yb, yb+1), outa / outb the destinations. The y faces ya-1/2, ya+1/2 and
+// yb+1/2 are formed once for the pair.
 template <int PP>
 __device__ __forceinline__ void march_emit(March& m, const float* P0,
                                            const uint8_t* S0, int cp,
@@ -220,20 +243,30 @@ __device__ __forceinline__ void march_emit(March& m, const float* P0,
   // phi along y at rows ya-2 .. yb+2 of the own column
   const float py0 = P0[cp - 2 * PP], py1 = P0[cp - PP], py4 = P0[cp + 2 * PP],
               py5 = P0[cp + 3 * PP];
+  const float va = m.ca[0], vb = m.cb[0];
   const bool sy0 = (S0[cp - PP] & FLAG_SOLID) != 0;
   const bool sy3 = (S0[cp + 2 * PP] & FLAG_SOLID) != 0;
-  if (act_a)
-    march_node(m.msum, m.wsum, P0, S0, cp, m.ca5[2], m.ca5[0], m.ca5[1], m.ca5[3],
-               m.ca5[4], m.sa3[1], m.sa3[0], m.sa3[2], py0, py1, m.cb5[2], py4,
-               sy0, m.sb3[1], uxa[0], uxa[1], uxa[2], uy4[0], uy4[1], uy4[2],
-               m.uza[0], m.uza[1], m.uza[2], m.Ha[0], m.Ha[1], m.Ha[2], m.Va[0],
-               m.Va[2], m.La[0], m.La[1], m.La[2], outa, k);
-  if (act_b)
-    march_node(m.msum, m.wsum, P0, S0, cp + PP, m.cb5[2], m.cb5[0], m.cb5[1],
-               m.cb5[3], m.cb5[4], m.sb3[1], m.sb3[0], m.sb3[2], py1, m.ca5[2],
-               py4, py5, m.sa3[1], sy3, uxb[0], uxb[1], uxb[2], uy4[1], uy4[2],
-               uy4[3], m.uzb[0], m.uzb[1], m.uzb[2], m.Hb[0], m.Hb[1], m.Hb[2],
-               m.Vb[0], m.Vb[2], m.Lb[0], m.Lb[1], m.Lb[2], outb, k);
+  const float s_m = minmod(py1 - py0, va - py1);  // y slopes at ya-1 .. yb+1
+  const float s_a = minmod(va - py1, vb - va);
+  const float s_b = minmod(vb - va, py4 - vb);
+  const float s_p = minmod(py4 - vb, py5 - py4);
+  const float fy_m = face_flux(uy4[0], uy4[1], py1, s_m, va, s_a);  // ya-1/2
+  const float fy_c = face_flux(uy4[1], uy4[2], va, s_a, vb, s_b);   // ya+1/2
+  const float fy_p = face_flux(uy4[2], uy4[3], vb, s_b, py4, s_p);  // yb+1/2
+  if (act_a) {
+    const float dy = (m.sb3[1] ? 0.f : fy_c) - (sy0 ? 0.f : fy_m);
+    const float dz = (m.sa3[2] ? 0.f : m.fzpa) - (m.sa3[0] ? 0.f : m.fzma);
+    march_node(m.msum, m.wsum, P0, S0, cp, va, m.sa3[1], dy, dz, uxa[0], uxa[1],
+               uxa[2], m.Ha[0], m.Ha[1], m.Ha[2], m.Va[0], m.Va[2], m.La[0],
+               m.La[1], m.La[2], outa, k);
+  }
+  if (act_b) {
+    const float dy = (sy3 ? 0.f : fy_p) - (m.sa3[1] ? 0.f : fy_c);
+    const float dz = (m.sb3[2] ? 0.f : m.fzpb) - (m.sb3[0] ? 0.f : m.fzmb);
+    march_node(m.msum, m.wsum, P0, S0, cp + PP, vb, m.sb3[1], dy, dz, uxb[0],
+               uxb[1], uxb[2], m.Hb[0], m.Hb[1], m.Hb[2], m.Vb[0], m.Vb[2],
+               m.Lb[0], m.Lb[1], m.Lb[2], outb, k);
+  }
 }
 
 // Block reduction of the two partial sums; thread 0 writes them as FP64 to
@@ -381,21 +414,22 @@ __device__ __forceinline__ void phase_tile_body(
   __syncthreads();
   March m;
   march_init(m);
-  m.ca5[3] = s_phi[(z0 - 2) & 3][cp];
-  m.ca5[4] = s_phi[(z0 - 1) & 3][cp];
-  m.cb5[3] = s_phi[(z0 - 2) & 3][cp + PX];
-  m.cb5[4] = s_phi[(z0 - 1) & 3][cp + PX];
-  // z velocity of the own columns: rolled, with the next plane's in nza/nzb
+  m.ca[1] = s_phi[(z0 - 2) & 3][cp];
+  m.ca[2] = s_phi[(z0 - 1) & 3][cp];
+  m.cb[1] = s_phi[(z0 - 2) & 3][cp + PX];
+  m.cb[2] = s_phi[(z0 - 1) & 3][cp + PX];
+  // z velocity of the own columns at kz, kz + 1 (rolled at the output
+  // planes), with the next plane's in nza / nzb
   const float* uz_ = u + 2 * N;
   float nza, nzb;
   {
     const int64_t zm = (int64_t)mod(z0 - 1, g.nz) * nxy;
     const int64_t zc = (int64_t)mod(z0, g.nz) * nxy;
     const int64_t zn = (int64_t)mod(z0 + 1, g.nz) * nxy;
-    m.uza[1] = __ldg(uz_ + zm + own_a);
-    m.uzb[1] = __ldg(uz_ + zm + own_b);
-    m.uza[2] = __ldg(uz_ + zc + own_a);
-    m.uzb[2] = __ldg(uz_ + zc + own_b);
+    m.uza[0] = __ldg(uz_ + zm + own_a);
+    m.uzb[0] = __ldg(uz_ + zm + own_b);
+    m.uza[1] = __ldg(uz_ + zc + own_a);
+    m.uzb[1] = __ldg(uz_ + zc + own_b);
     nza = __ldg(uz_ + zn + own_a);
     nzb = __ldg(uz_ + zn + own_b);
   }
@@ -440,8 +474,8 @@ __device__ __forceinline__ void phase_tile_body(
 #pragma unroll
     for (int i = 0; i < 4; ++i) uy4[i] = ny4[i];
     if (out) {
-      m.uza[0] = m.uza[1]; m.uza[1] = m.uza[2]; m.uza[2] = nza;
-      m.uzb[0] = m.uzb[1]; m.uzb[1] = m.uzb[2]; m.uzb[2] = nzb;
+      m.uza[0] = m.uza[1]; m.uza[1] = nza;
+      m.uzb[0] = m.uzb[1]; m.uzb[1] = nzb;
       const int z2 = (kz + 2 >= g.nz) ? kz + 2 - g.nz : kz + 2;
       nza = __ldg(uz_ + (int64_t)z2 * nxy + own_a);
       nzb = __ldg(uz_ + (int64_t)z2 * nxy + own_b);
@@ -496,7 +530,10 @@ constexpr int NCH = CW / 4;
 template <int TY, int D>
 struct CopyTile {
   static constexpr int PR = TY + 4, AR = TY + 2;
-  static constexpr int RP = 4 + D, RA = 2 + D;
+  // ring sizes: at least 4 + D phi planes and 2 + D a / u planes, rounded
+  // up to powers of two so that slots are plane counters masked
+  static constexpr int RP = (4 + D <= 4) ? 4 : (4 + D <= 8 ? 8 : 16);
+  static constexpr int RA = (2 + D <= 2) ? 2 : (2 + D <= 4 ? 4 : 8);
   static constexpr int PHI = PR * CW;               // floats per phi slot
   static constexpr int AC = AR * CW;                // floats per a component
   static constexpr int UX = TY * CW, UY = (TY + 2) * TX, UZ = TY * TX;
@@ -551,7 +588,7 @@ __device__ __forceinline__ void phase_tile_copy(
 
   const int nb = zend - z0 + 2;  // bundles / steps: planes z0-2 .. zend-1
   auto issue_phi = [&](int p, int slot) {  // phi and flags of plane p
-    const int64_t zo = (int64_t)mod(p, g.nz) * nxy;
+    const int64_t zo = (int64_t)wrap1(p, g.nz) * nxy;
     if (hp) {
       cp_async16(s_phi + slot * L::PHI + sp, phi + zo + gp);
       cp_async4(s_flg + slot * L::FLG + sp, flags + zo + gp);
@@ -559,9 +596,9 @@ __device__ __forceinline__ void phase_tile_copy(
   };
   auto issue = [&](int b) {  // bundle b: step kz = z0 - 2 + b
     const int t = z0 - 2 + b;
-    issue_phi(t + 2, (b + 2) % L::RP);
-    float* sa = s_au + (b % L::RA) * L::ASLOT;
-    const int64_t z1 = (int64_t)mod(t + 1, g.nz) * nxy;
+    issue_phi(t + 2, (b + 2) & (L::RP - 1));
+    float* sa = s_au + (b & (L::RA - 1)) * L::ASLOT;
+    const int64_t z1 = (int64_t)wrap1(t + 1, g.nz) * nxy;
     if (ha) {
 #pragma unroll
       for (int c = 0; c < 3; ++c)
@@ -569,7 +606,7 @@ __device__ __forceinline__ void phase_tile_copy(
     }
     if (hz) cp_async16(sa + 3 * L::AC + L::UX + L::UY + s8, u + 2 * N + z1 + gz);
     if (b >= 2) {  // output plane t
-      const int64_t z0o = (int64_t)mod(t, g.nz) * nxy;
+      const int64_t z0o = (int64_t)wrap1(t, g.nz) * nxy;
       if (hx) cp_async16(sa + 3 * L::AC + sp, u + z0o + gx);
       if (hy) cp_async16(sa + 3 * L::AC + L::UX + s8, u + N + z0o + gy);
     }
@@ -606,22 +643,22 @@ __device__ __forceinline__ void phase_tile_copy(
     cp_async_commit();
     cp_async_wait<D>();
     __syncthreads();
-    const float* P0 = s_phi + (b % L::RP) * L::PHI;
-    const float* P1 = s_phi + ((b + 1) % L::RP) * L::PHI;
-    const float* P2 = s_phi + ((b + 2) % L::RP) * L::PHI;
-    const uint8_t* S0 = s_flg + (b % L::RP) * L::FLG;
-    const uint8_t* S1 = s_flg + ((b + 1) % L::RP) * L::FLG;
-    const float* sa = s_au + (b % L::RA) * L::ASLOT;
+    const float* P0 = s_phi + (b & (L::RP - 1)) * L::PHI;
+    const float* P1 = s_phi + ((b + 1) & (L::RP - 1)) * L::PHI;
+    const float* P2 = s_phi + ((b + 2) & (L::RP - 1)) * L::PHI;
+    const uint8_t* S0 = s_flg + (b & (L::RP - 1)) * L::FLG;
+    const uint8_t* S1 = s_flg + ((b + 1) & (L::RP - 1)) * L::FLG;
+    const float* sa = s_au + (b & (L::RA - 1)) * L::ASLOT;
     const float* su = sa + 3 * L::AC;
     if (b == 0) {  // own columns at planes z0-2, z0-1
-      m.ca5[3] = P0[cp];
-      m.cb5[3] = P0[cp + CW];
-      m.ca5[4] = P1[cp];
-      m.cb5[4] = P1[cp + CW];
+      m.ca[1] = P0[cp];
+      m.cb[1] = P0[cp + CW];
+      m.ca[2] = P1[cp];
+      m.cb[2] = P1[cp + CW];
     }
     const float* suz = su + L::UX + L::UY;
-    m.uza[0] = m.uza[1]; m.uza[1] = m.uza[2]; m.uza[2] = suz[czu];
-    m.uzb[0] = m.uzb[1]; m.uzb[1] = m.uzb[2]; m.uzb[2] = suz[czu + TX];
+    m.uza[0] = m.uza[1]; m.uza[1] = suz[czu];
+    m.uzb[0] = m.uzb[1]; m.uzb[1] = suz[czu + TX];
     march_roll<CW, CW>(m, P1, P2, S1, sa, sa + L::AC, sa + 2 * L::AC, cp, ca);
     if (b < 2) continue;
     const float uxa[3] = {su[cxu - 1], su[cxu], su[cxu + 1]};
@@ -740,6 +777,7 @@ int phase_blocks(const cacl_ctx* c) {
 
 namespace {
 // copy-staged kernels of the four tile shapes, with their shared memory
+// (plane indices are wrapped once, so nz >= 2)
 constexpr int COPY_D = 2;  // planes of copies in flight ahead of the compute
 struct CopyKernel {
   void* fn;
@@ -769,7 +807,7 @@ cudaError_t phase_init_attributes() {
 
 bool phase_copy_ok(const Grid& g, const void* phi_in, const void* phi_out,
                    const void* a, const void* u, const void* flags) {
-  return g.nx % 4 == 0 && aligned16(phi_in) && aligned16(phi_out) &&
+  return g.nx % 4 == 0 && g.nz >= 2 && aligned16(phi_in) && aligned16(phi_out) &&
          aligned16(a) && aligned16(u) && ((uintptr_t)flags & 3u) == 0;
 }
 
