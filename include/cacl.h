@@ -50,7 +50,8 @@ typedef enum {
   CACL_ERR_STATE = -3,     /* call out of the required order */
   CACL_ERR_GEOMETRY = -4,  /* non-periodic axis not closed by solid layers */
   CACL_ERR_DIVERGED = -5,  /* non-finite phi or u found by cacl_check_finite */
-  CACL_ERR_TIMEOUT = -6,   /* reserved for bounded device waits */
+  CACL_ERR_TIMEOUT = -6,   /* a bounded device wait gave up (reported by
+                              cacl_check_finite) */
   CACL_ERR_TOO_LARGE = -7  /* size above the fixed scratch of an
                               allocation-free entry point */
 } cacl_status;
@@ -150,8 +151,9 @@ cacl_status cacl_step(cacl_ctx* ctx, int nsteps);
 /* The four parts of one step, enqueued singly (for inspection and part by
  * part checks). cacl_lb_collide reads phi and writes populations, u and the
  * compressive vector of phi; cacl_phase_update forms that vector from the
- * current phi itself, then writes phi* and the block partial sums;
- * cacl_volume_correct forms lambda and phi^{n+1} = phi* + lambda chi(phi*). */
+ * current phi itself, then writes phi*, the block partial sums and, from
+ * them, lambda; cacl_volume_correct writes
+ * phi^{n+1} = phi* + lambda chi(phi*). */
 cacl_status cacl_ghost_update(cacl_ctx* ctx);
 cacl_status cacl_lb_collide(cacl_ctx* ctx);
 cacl_status cacl_phase_update(cacl_ctx* ctx);
@@ -176,7 +178,10 @@ cacl_status cacl_get_wall_list(cacl_ctx* ctx, int32_t* idx, int8_t* qstar,
 cacl_status cacl_get_mass(cacl_ctx* ctx, double* m_ref, double* m_star,
                           double* w_sum, double* lambda);
 
-/* Returns CACL_ERR_DIVERGED if phi or u holds a NaN or Inf. Synchronises. */
+/* Returns CACL_ERR_TIMEOUT if a kernel's bounded wait for its asynchronous
+ * copies gave up since the context was created (its results are then not
+ * to be trusted), else CACL_ERR_DIVERGED if phi or u holds a NaN or Inf.
+ * Synchronises. */
 cacl_status cacl_check_finite(cacl_ctx* ctx);
 
 /*
@@ -246,9 +251,18 @@ cacl_status cacl_batch_autotune(cacl_batch* batch, int steps, int* lb_variant,
  * when nx is a multiple of 4 and the fields are 16-byte aligned, else
  * staging through registers), 1 = registers, 2 = asynchronous copies
  * (CACL_ERR_ARG when nx is not a multiple of 4 or nz < 2). Both give
- * bit-identical results. Returns CACL_ERR_ARG for an unknown option or
- * value. */
-typedef enum { CACL_OPT_PHASE_TILE = 1, CACL_OPT_PHASE_PIPE = 2 } cacl_option;
+ * bit-identical results. CACL_OPT_LB_PIPE selects how the collide-stream
+ * reads its 27 pulled population rows and 9 phi rows: 0 = direct loads
+ * through the cache (the default), 1 = row runs staged in shared memory by
+ * bulk asynchronous copies through a two-stage ring of persistent blocks
+ * (CACL_ERR_ARG unless nx is a multiple of 4 and of 16 bytes' worth of
+ * populations); bit-identical results. Defaults: tile 2, pipelines 0.
+ * Returns CACL_ERR_ARG for an unknown option or value. */
+typedef enum {
+  CACL_OPT_PHASE_TILE = 1,
+  CACL_OPT_PHASE_PIPE = 2,
+  CACL_OPT_LB_PIPE = 3
+} cacl_option;
 cacl_status cacl_set_option(cacl_ctx* ctx, int option, int value);
 
 /* Grid size N and bytes of device memory the context holds. */

@@ -35,6 +35,7 @@ EXPORTS = (
 )
 OPT_PHASE_TILE = 1
 OPT_PHASE_PIPE = 2  # 0 auto, 1 register staging, 2 asynchronous copies
+OPT_LB_PIPE = 3  # 0 direct loads, 1 bulk-copy staged rows
 
 
 class CaclError(RuntimeError):

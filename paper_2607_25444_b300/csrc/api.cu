@@ -149,6 +149,7 @@ cacl_status cacl_create(const cacl_params* p, void* stream, cacl_ctx** out) {
     c->own_stream = true;
   }
   if ((e = phase_init_attributes()) != cudaSuccess) return bail("attributes");
+  if ((e = lb_init(c)) != cudaSuccess) return bail("collide-stream set-up");
   const size_t fbytes = storage_bytes(p->storage) * (size_t)Q * N;
   for (int i = 0; i < 2; ++i) {
     if ((e = cudaMalloc(&c->f[i], fbytes)) != cudaSuccess) return bail("alloc f");
@@ -168,6 +169,11 @@ cacl_status cacl_create(const cacl_params* p, void* stream, cacl_ctx** out) {
     return bail("alloc mass");
   if ((e = cudaMalloc(&c->bad_flag, sizeof(int))) != cudaSuccess)
     return bail("alloc flag");
+  if ((e = cudaMalloc(&c->ticket, 2 * sizeof(unsigned))) != cudaSuccess)
+    return bail("alloc ticket");
+  if ((e = cudaMemsetAsync(c->ticket, 0, 2 * sizeof(unsigned), c->stream)) !=
+      cudaSuccess)
+    return bail("memset");
   if ((e = cudaMemsetAsync(c->mass, 0, sizeof(MassScalars), c->stream)) !=
       cudaSuccess)
     return bail("memset");
@@ -187,7 +193,7 @@ void cacl_destroy(cacl_ctx* c) {
   void* bufs[] = {c->f[0], c->f[1], c->phi[0], c->phi[1], c->u, c->a, c->flags,
                   c->w_idx, c->w_donor, c->w_q, c->w_n6, c->w_nw, c->w_cot,
                   c->w_theta, c->w_g, c->partials, c->mass, c->scan_scratch,
-                  c->bad_flag};
+                  c->bad_flag, c->ticket};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -468,11 +474,15 @@ cacl_status cacl_get_mass(cacl_ctx* c, double* m_ref, double* m_star,
 cacl_status cacl_check_finite(cacl_ctx* c) {
   if (!ready(c)) return c ? CACL_ERR_STATE : CACL_ERR_ARG;
   int bad = 0;
+  unsigned waited = 0;
   CK(cudaMemsetAsync(c->bad_flag, 0, sizeof(int), c->stream), "memset");
   CK(launch_check_finite(c, c->phi[c->pcur], c->bad_flag), "finite check");
   CK(cudaMemcpyAsync(&bad, c->bad_flag, sizeof(int), cudaMemcpyDeviceToHost,
                      c->stream), "copy flag");
+  CK(cudaMemcpyAsync(&waited, c->ticket + 1, sizeof(unsigned),
+                     cudaMemcpyDeviceToHost, c->stream), "copy flag");
   CK(cudaStreamSynchronize(c->stream), "sync");
+  if (waited) return fail(c, CACL_ERR_TIMEOUT, "a wait for asynchronous copies gave up");
   if (bad) return fail(c, CACL_ERR_DIVERGED, "non-finite phi or u");
   return CACL_OK;
 }
@@ -483,6 +493,15 @@ cacl_status cacl_set_option(cacl_ctx* c, int option, int value) {
     if (value < 0 || value > 3) return fail(c, CACL_ERR_ARG, "unknown phase tile");
     if (c->phase_variant != value) drop_graphs(c);
     c->phase_variant = value;
+    return CACL_OK;
+  }
+  if (option == CACL_OPT_LB_PIPE) {
+    if (value < 0 || value > 1) return fail(c, CACL_ERR_ARG, "unknown collide pipeline");
+    const int pf = 16 / (int)storage_bytes(c->p.storage);
+    if (value == 1 && (c->g.nx % pf != 0 || c->g.nx % 4 != 0))
+      return fail(c, CACL_ERR_ARG, "staged collide-stream needs nx a multiple of 16 bytes");
+    if (c->lb_pipe != value) drop_graphs(c);
+    c->lb_pipe = value;
     return CACL_OK;
   }
   if (option == CACL_OPT_PHASE_PIPE) {

@@ -19,7 +19,7 @@ struct cacl_batch {
   bool own_stream = false;
   int storage = CACL_F32;
   int lb_variant = 1;
-  int phase_variant = 0;
+  int phase_variant = 2;
   CaseDesc* d_cases = nullptr;
   int* d_starts = nullptr;  // four lists of ncases + 1 starts
   WorkList wl_lb{}, wl_phase{}, wl_ghost{}, wl_corr{};

@@ -40,10 +40,13 @@ __host__ __device__ constexpr float wq(int q) {
 // / w_i with p*_ref = 0 (the pressure gauge of the initial state), rounded
 // to nearest even; 1/w_i is exact in FP32, so the scaling adds no rounding.
 // All arithmetic stays FP32.
+// Population storage: decode gives f_q, encode stores f_q, and encode_w
+// stores the population w_q P given P = f_q / w_q.
 struct StoreF32 {
   using T = float;
   __device__ __forceinline__ static float decode(T v, int q) { return v; }
   __device__ __forceinline__ static T encode(float v, int q) { return v; }
+  __device__ __forceinline__ static T encode_w(float P, int q) { return wq(q) * P; }
 };
 
 struct StoreF16 {
@@ -54,6 +57,9 @@ struct StoreF16 {
   __device__ __forceinline__ static T encode(float v, int q) {
     return __float2half_rn(v * (1.0f / wq(q)));
   }
+  __device__ __forceinline__ static T encode_w(float P, int q) {
+    return __float2half_rn(P);
+  }
 };
 
 struct StoreBF16 {
@@ -63,6 +69,9 @@ struct StoreBF16 {
   }
   __device__ __forceinline__ static T encode(float v, int q) {
     return __float2bfloat16_rn(v * (1.0f / wq(q)));
+  }
+  __device__ __forceinline__ static T encode_w(float P, int q) {
+    return __float2bfloat16_rn(P);
   }
 };
 
@@ -86,6 +95,21 @@ __device__ __forceinline__ int wrap(int i, int d, int n) {
   return (j >= n) ? j - n : j;
 }
 
+// One pair of opposite links (q, 26 - q) of the isotropic phi stencil (Eqs.
+// grad_iso, lap_iso): phi at x + c_q (vp) and x - c_q (vm) added to the
+// gradient and to sum_q w_q phi(x + c_q), in explicitly rounded operations.
+__device__ __forceinline__ void stencil_pair(int q, float vp, float vm, float& gx,
+                                             float& gy, float& gz, float& ssum) {
+  const float dv = __fmul_rn(3.0f * wq(q), __fadd_rn(vp, -vm));
+  if (cx(q) > 0) gx = __fadd_rn(gx, dv);
+  if (cx(q) < 0) gx = __fadd_rn(gx, -dv);
+  if (cy(q) > 0) gy = __fadd_rn(gy, dv);
+  if (cy(q) < 0) gy = __fadd_rn(gy, -dv);
+  if (cz(q) > 0) gz = __fadd_rn(gz, dv);
+  if (cz(q) < 0) gz = __fadd_rn(gz, -dv);
+  ssum = fmaf(wq(q), __fadd_rn(vp, vm), ssum);
+}
+
 // Isotropic gradient (Eq. grad_iso) and the neighbour sum of Eq. lap_iso of
 // phi at a node whose wrapped neighbour offsets are xo/yo/zo[0..2] (-1, 0,
 // +1), summed over pairs of opposite links. lap = 6 (ssum - (1 - w_0) phi).
@@ -103,11 +127,7 @@ __device__ __forceinline__ void phi_stencil(const float* __restrict__ phi,
   for (int q = 0; q < REST; ++q) {
     const float vp = __ldg(phi + xo[1 + cx(q)] + yo[1 + cy(q)] + zo[1 + cz(q)]);
     const float vm = __ldg(phi + xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)]);
-    const float dv = (3.0f * wq(q)) * (vp - vm);
-    gx += cx(q) * dv;
-    gy += cy(q) * dv;
-    gz += cz(q) * dv;
-    ssum += wq(q) * (vp + vm);
+    stencil_pair(q, vp, vm, gx, gy, gz, ssum);
   }
 }
 
@@ -116,13 +136,13 @@ __device__ __forceinline__ void phi_stencil(const float* __restrict__ phi,
 __device__ __forceinline__ void compressive(float phi0, float gx, float gy,
                                             float gz, float& ax, float& ay,
                                             float& az) {
-  const float g2 = gx * gx + gy * gy + gz * gz;
+  const float g2 = fmaf(gz, gz, fmaf(gy, gy, __fmul_rn(gx, gx)));
   ax = ay = az = 0.f;
   if (g2 >= 1e-24f) {
-    const float sc = phi0 * (1.0f - phi0) * rsqrtf(g2);
-    ax = sc * gx;
-    ay = sc * gy;
-    az = sc * gz;
+    const float sc = __fmul_rn(__fmul_rn(phi0, __fadd_rn(1.0f, -phi0)), rsqrtf(g2));
+    ax = __fmul_rn(sc, gx);
+    ay = __fmul_rn(sc, gy);
+    az = __fmul_rn(sc, gz);
   }
 }
 
@@ -169,6 +189,39 @@ __device__ __forceinline__ float add_unbiased(float s, float d, uint32_t step,
   const float u = (float)(z >> 40) * (1.0f / 16777216.0f);
   const float nb = nextafterf(t, e > 0.f ? INFINITY : -INFINITY);
   return (u * fabsf(nb - t) < fabsf(e)) ? nb : t;
+}
+
+// Fixed-order sum of nb doubles by one warp: lane l adds src[l], src[l+32],
+// ... in turn, then the lanes combine pairwise (offsets 16, 8, 4, 2, 1).
+// The loads go through L2 (ld.global.cg): the values may have been written
+// by other blocks of the same launch. The result is valid in lane 0.
+__device__ __forceinline__ double warp_sum_fixed(const double* src, int nb,
+                                                 int lane) {
+  double s = 0.0;
+#pragma unroll 8
+  for (int i = lane; i < nb; i += 32) s += __ldcg(src + i);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  return s;
+}
+
+// lambda = (M_ref - M*) / W of the volume correction (Eq.
+// mass_correction_normalization; 0 when W = 0) from the per-block partial
+// sums of the phi update (nb phi* sums, then nb chi sums), by warp 0 of the
+// calling block; the correction counter advances by one.
+__device__ __forceinline__ void mass_from_partials(const double* partials,
+                                                   int nb, MassScalars* ms,
+                                                   int lane) {
+  const double m = warp_sum_fixed(partials, nb, lane);
+  const double w = warp_sum_fixed(partials + nb, nb, lane);
+  if (lane == 0) {
+    const double lam = (w > 0.0) ? (ms->m_ref - m) / w : 0.0;
+    ms->m_star = m;
+    ms->w_sum = w;
+    ms->lambda = lam;
+    ms->lambda_f = (float)lam;
+    ms->step += 1;
+  }
 }
 
 // One case of a batch as the batched kernels see it: grid, constants and
@@ -284,8 +337,10 @@ struct cacl_ctx {
   float* w_g = nullptr;     // ghost scratch
 
   // kernel shape choices (cacl_set_option)
-  int phase_variant = 0;
+  int phase_variant = 2;
   int phase_pipe = 0;      // 0 auto, 1 register staging, 2 cp.async staging
+  int lb_pipe = 0;         // 0 direct loads, 1 bulk-copy staged rows
+  int lb_grid = 1;         // blocks of the persistent staged collide-stream
   int phase_nblocks = 0;   // blocks of the last phase-update launch
 
   // reductions
@@ -298,6 +353,9 @@ struct cacl_ctx {
   // one-step graphs, indexed by (fcur, pcur)
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   int* bad_flag = nullptr;  // device word for cacl_check_finite
+  // [0] phase-update blocks done (the last one finalises), [1] set when a
+  // bounded wait for asynchronous copies gave up
+  unsigned* ticket = nullptr;
   AdjointState* adj = nullptr;  // checkpoints, tape and adjoint fields
   int64_t device_bytes = 0;
 };
@@ -306,6 +364,9 @@ struct cacl_ctx {
 namespace cacl {
 cudaError_t launch_geometry(cacl_ctx* c, const uint8_t* solid_dev);
 cudaError_t launch_ghost(cacl_ctx* c, float* phi);
+cudaError_t lb_init(cacl_ctx* c);
+bool lb_staged_ok(const cacl_ctx* c, const void* fin, const void* fout,
+                  const void* phi);
 cudaError_t launch_lb(cacl_ctx* c, const void* fin, void* fout,
                       const float* phi);
 cudaError_t launch_compressive(cacl_ctx* c, const float* phi);

@@ -298,6 +298,24 @@ __device__ __forceinline__ void block_partials(DF msum, DF wsum, int tid,
   }
 }
 
+// After the block's partial sums are stored: the last block of the launch
+// to finish (a ticket counter, no waiting) forms lambda from all partials
+// and resets the counter for the next launch.
+__device__ __forceinline__ void finish_mass(const double* partials, int nb,
+                                            MassScalars* ms, unsigned* ticket,
+                                            int tid) {
+  __shared__ bool last;
+  if (tid == 0) {
+    __threadfence();  // this block's partials before its ticket
+    last = atomicAdd(ticket, 1u) == (unsigned)(nb - 1);
+  }
+  __syncthreads();
+  if (!last || tid >= 32) return;
+  __threadfence();
+  mass_from_partials(partials, nb, ms, tid);
+  if (tid == 0) *ticket = 0u;
+}
+
 // One block: TX x TY output nodes per plane, TX x TY/2 threads; each thread
 // owns two vertically adjacent output nodes (rows 2 ty and 2 ty + 1), which
 // share most of their stencil reads and all per-thread bookkeeping.
@@ -679,10 +697,11 @@ phase_update_march(const float* __restrict__ phi, const float* __restrict__ afld
                    float* __restrict__ phi_out, const float* __restrict__ u,
                    const uint8_t* __restrict__ flags,
                    double* __restrict__ partials, int nblocks, Grid g,
-                   Consts k) {
+                   Consts k, MassScalars* ms, unsigned* ticket) {
   const int pb = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   phase_tile_body<TY, ZC>(blockIdx.x, blockIdx.y, blockIdx.z, pb, phi, afld,
                           phi_out, u, flags, partials, nblocks, g, k);
+  finish_mass(partials, nblocks, ms, ticket, threadIdx.x + TX * threadIdx.y);
 }
 
 template <int TY, int ZC, int D, int MINB>
@@ -691,11 +710,12 @@ phase_update_copy(const float* __restrict__ phi, const float* __restrict__ afld,
                   float* __restrict__ phi_out, const float* __restrict__ u,
                   const uint8_t* __restrict__ flags,
                   double* __restrict__ partials, int nblocks, Grid g,
-                  Consts k) {
+                  Consts k, MassScalars* ms, unsigned* ticket) {
   extern __shared__ __align__(16) float dsm[];
   const int pb = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   phase_tile_copy<TY, ZC, D>(blockIdx.x, blockIdx.y, blockIdx.z, pb, phi, afld,
                              phi_out, u, flags, partials, nblocks, g, k, dsm);
+  finish_mass(partials, nblocks, ms, ticket, threadIdx.x + TX * threadIdx.y);
 }
 
 // Batched phi update: virtual block b is tile (bx, by, bz) of its case.
@@ -869,26 +889,34 @@ cudaError_t launch_phase(cacl_ctx* c, const float* phi_in, float* phi_out) {
     Grid g = c->g;
     Consts k = c->k;
     int nbk = nb;
-    void* args[] = {(void*)&phi_in, (void*)&a, (void*)&phi_out, (void*)&u,
-                    (void*)&fl, (void*)&part, (void*)&nbk, (void*)&g, (void*)&k};
+    MassScalars* ms = c->mass;
+    unsigned* ticket = c->ticket;
+    void* args[] = {(void*)&phi_in, (void*)&a,    (void*)&phi_out,
+                    (void*)&u,      (void*)&fl,   (void*)&part,
+                    (void*)&nbk,    (void*)&g,    (void*)&k,
+                    (void*)&ms,     (void*)&ticket};
     return cudaLaunchKernel(ck.fn, grid, block, args, ck.smem, c->stream);
   }
   switch (v) {
     case 1:
       phase_update_march<8, 16, 4><<<grid, block, 0, c->stream>>>(
-          phi_in, c->a, phi_out, c->u, c->flags, c->partials, nb, c->g, c->k);
+          phi_in, c->a, phi_out, c->u, c->flags, c->partials, nb, c->g, c->k,
+          c->mass, c->ticket);
       break;
     case 2:
       phase_update_march<8, 32, 4><<<grid, block, 0, c->stream>>>(
-          phi_in, c->a, phi_out, c->u, c->flags, c->partials, nb, c->g, c->k);
+          phi_in, c->a, phi_out, c->u, c->flags, c->partials, nb, c->g, c->k,
+          c->mass, c->ticket);
       break;
     case 3:
       phase_update_march<16, 32, 2><<<grid, block, 0, c->stream>>>(
-          phi_in, c->a, phi_out, c->u, c->flags, c->partials, nb, c->g, c->k);
+          phi_in, c->a, phi_out, c->u, c->flags, c->partials, nb, c->g, c->k,
+          c->mass, c->ticket);
       break;
     default:
       phase_update_march<16, 16, 2><<<grid, block, 0, c->stream>>>(
-          phi_in, c->a, phi_out, c->u, c->flags, c->partials, nb, c->g, c->k);
+          phi_in, c->a, phi_out, c->u, c->flags, c->partials, nb, c->g, c->k,
+          c->mass, c->ticket);
       break;
   }
   return cudaGetLastError();

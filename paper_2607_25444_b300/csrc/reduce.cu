@@ -4,52 +4,21 @@
 // reference (Eq. phase_field_mass) and small state queries.
 //
 // The correction is deterministic: the phase update leaves one FP64 pair
-// (sum phi*, sum chi) per block; finalize_mass sums them in a fixed order in
-// one block and forms lambda = (M_ref - M*)/W (0 when W = 0);
-// correct_phi applies phi = phi* + lambda chi(phi*) at fluid nodes.
+// (sum phi*, sum chi) per block, and its last block to finish sums them in
+// a fixed order and forms lambda = (M_ref - M*)/W (0 when W = 0; the
+// batched path does the same in finalize_mass_batch); correct_phi applies
+// phi = phi* + lambda chi(phi*) at fluid nodes.
 #include "cacl_internal.cuh"
 
 namespace cacl {
 namespace {
 
-constexpr int FIN_THREADS = 1024;
 constexpr int ELEM_THREADS = 256;
 
-// Fixed-order sum of nb doubles at src (strided per thread, then a tree).
-__device__ double block_sum(const double* src, int nb, double* sh) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nb; i += FIN_THREADS) s += src[i];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = FIN_THREADS / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  const double r = sh[0];
-  __syncthreads();
-  return r;
-}
-
-__global__ void __launch_bounds__(FIN_THREADS)
-finalize_mass(const double* __restrict__ partials, int nb, MassScalars* ms) {
-  __shared__ double sh[FIN_THREADS];
-  const double m = block_sum(partials, nb, sh);
-  const double w = block_sum(partials + nb, nb, sh);
-  if (threadIdx.x == 0) {
-    const double lam = (w > 0.0) ? (ms->m_ref - m) / w : 0.0;
-    ms->m_star = m;
-    ms->w_sum = w;
-    ms->lambda = lam;
-    ms->lambda_f = (float)lam;
-    ms->step += 1;
-  }
-}
-
-__global__ void __launch_bounds__(FIN_THREADS)
+__global__ void __launch_bounds__(32)
 finalize_mass_ref(const double* __restrict__ partials, int nb,
                   MassScalars* ms) {
-  __shared__ double sh[FIN_THREADS];
-  const double m = block_sum(partials, nb, sh);
+  const double m = warp_sum_fixed(partials, nb, threadIdx.x);
   if (threadIdx.x == 0) {
     ms->m_ref = m;
     ms->m_star = m;
@@ -60,22 +29,11 @@ finalize_mass_ref(const double* __restrict__ partials, int nb,
   }
 }
 
-// Batched finalize: block c reduces case c's partials.
-__global__ void __launch_bounds__(FIN_THREADS)
+// Batched finalize: block c (one warp) reduces case c's partials.
+__global__ void __launch_bounds__(32)
 finalize_mass_batch(const CaseDesc* __restrict__ cases) {
-  __shared__ double sh[FIN_THREADS];
   const CaseDesc& cd = cases[blockIdx.x];
-  const double m = block_sum(cd.partials, cd.phase_nb, sh);
-  const double w = block_sum(cd.partials + cd.phase_nb, cd.phase_nb, sh);
-  if (threadIdx.x == 0) {
-    MassScalars* ms = cd.mass;
-    const double lam = (w > 0.0) ? (ms->m_ref - m) / w : 0.0;
-    ms->m_star = m;
-    ms->w_sum = w;
-    ms->lambda = lam;
-    ms->lambda_f = (float)lam;
-    ms->step += 1;
-  }
+  mass_from_partials(cd.partials, cd.phase_nb, cd.mass, threadIdx.x);
 }
 
 // phi = phi* + lambda chi(phi*) at fluid nodes, four nodes per thread,
@@ -235,8 +193,7 @@ int elem_blocks(int64_t N) { return (int)((N + ELEM_THREADS - 1) / ELEM_THREADS)
 }  // namespace
 
 cudaError_t launch_correct(cacl_ctx* c, float* phi) {
-  finalize_mass<<<1, FIN_THREADS, 0, c->stream>>>(c->partials,
-                                                 c->phase_nblocks, c->mass);
+  // lambda was formed by the last block of the phi update
   const int64_t N = c->g.N;
   const int nb = (int)((N + 4 * ELEM_THREADS - 1) / (4 * ELEM_THREADS));
   correct_phi<<<nb, ELEM_THREADS, 0, c->stream>>>(phi, c->flags, c->mass, N,
@@ -248,7 +205,7 @@ int correct_batch_nodes() { return 4 * ELEM_THREADS; }
 
 cudaError_t launch_correct_batch(const CaseDesc* cases, int ncases, WorkList wl,
                                  int grid, int pc, cudaStream_t st) {
-  finalize_mass_batch<<<ncases, FIN_THREADS, 0, st>>>(cases);
+  finalize_mass_batch<<<ncases, 32, 0, st>>>(cases);
   correct_phi_batch<<<grid, ELEM_THREADS, 0, st>>>(cases, wl, pc);
   return cudaGetLastError();
 }
@@ -257,7 +214,7 @@ cudaError_t launch_mass_ref(cacl_ctx* c, const float* phi) {
   const int64_t N = c->g.N;
   const int nb = (int)((N + ELEM_THREADS * 8 - 1) / (ELEM_THREADS * 8));
   fluid_sum<<<nb, ELEM_THREADS, 0, c->stream>>>(phi, c->flags, N, c->partials);
-  finalize_mass_ref<<<1, FIN_THREADS, 0, c->stream>>>(c->partials, nb, c->mass);
+  finalize_mass_ref<<<1, 32, 0, c->stream>>>(c->partials, nb, c->mass);
   return cudaGetLastError();
 }
 

@@ -324,6 +324,33 @@ def test_phase_copy_pipeline_rejects_unaligned_nx():
     g.set_option(cacl.OPT_PHASE_PIPE, 0)
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("shape", [(144, 10, 9), (16, 12, 10)])
+def test_lb_staged_pipeline(storage, shape):
+    """The collide-stream reading its pulled rows from bulk asynchronous
+    copies gives bit for bit the populations, u and phi of direct loads over
+    20 full steps: a partial last row segment (nx = 144 = 128 + 16) and a
+    row narrower than the 16-byte pads' reach (both pads wrap)."""
+    from paper_2607_25444_b300 import cacl
+    nx, ny, nz = shape
+    p, solid, phi = _droplet_case(nx=nx, ny=ny, nz=nz, theta=70.0)
+    p = dict(p, storage=storage)
+    u = I.fast_uniform((3, nz, ny, nx), seed=5, lo=-0.02, hi=0.02).astype(np.float32)
+    u[:, solid == 1] = 0.0
+    runs = []
+    for pipe in (0, 1):
+        g = _solver(p)
+        g.set_option(cacl.OPT_LB_PIPE, pipe)
+        g.set_geometry(solid)
+        g.set_fields(phi, u)
+        g.step(20)
+        g.check_finite()
+        ph, uu, _ = g.fields()
+        runs.append((ph, uu, g.populations()))
+    for a, b in zip(runs[0], runs[1]):
+        assert np.array_equal(a, b)
+
+
 def _quantize(f, storage):
     """Round f_i / w_i to the 16-bit storage (nearest even) and scale back."""
     import torch
