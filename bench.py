@@ -405,7 +405,9 @@ def run_cuda(args):
     s.set_geometry(solid)
     s.set_fields(phi)
     W = s.info()["wall_count"]
-    kernels_per_step = 4 + (2 if W > 0 else 0)
+    # collide-stream, phi update (its last block forms lambda), correction,
+    # and the two ghost passes when there are walls
+    kernels_per_step = 3 + (2 if W > 0 else 0)
 
     # warm-up, then K timed steps bracketed by barrier + synchronize
     s.step(args.warmup)
