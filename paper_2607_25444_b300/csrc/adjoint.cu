@@ -58,20 +58,24 @@ adj_correct_sum(const float* __restrict__ phib, const float* __restrict__ phis,
   if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
 }
 
+// S / W and lambda for the apply pass, once per step: one warp sums the
+// block partials of S in a fixed order.
+__global__ void __launch_bounds__(32)
+adj_correct_scalars(const double* __restrict__ partial, int nparts,
+                    const MassScalars* __restrict__ ms, float* __restrict__ out) {
+  const double S = warp_sum_fixed(partial, nparts, threadIdx.x);
+  if (threadIdx.x == 0) {
+    const double W = ms->w_sum;
+    out[0] = (W > 0.0) ? (float)(S / W) : 0.f;
+    out[1] = (W > 0.0) ? ms->lambda_f : 0.f;
+  }
+}
+
 __global__ void __launch_bounds__(AT)
 adj_correct_apply(const float* __restrict__ phib, const float* __restrict__ phis,
                   const uint8_t* __restrict__ flags, int64_t N, float eps,
-                  const double* __restrict__ partial, int nparts,
-                  const MassScalars* __restrict__ ms, float* __restrict__ phisb) {
-  __shared__ float s_over_w, lam;
-  if (threadIdx.x == 0) {
-    double S = 0.0;
-    for (int i = 0; i < nparts; ++i) S += partial[i];
-    const double W = ms->w_sum;
-    s_over_w = (W > 0.0) ? (float)(S / W) : 0.f;
-    lam = (W > 0.0) ? ms->lambda_f : 0.f;
-  }
-  __syncthreads();
+                  const float* __restrict__ scal, float* __restrict__ phisb) {
+  const float s_over_w = scal[0], lam = scal[1];
   const int64_t n = (int64_t)blockIdx.x * AT + threadIdx.x;
   if (n >= N) return;
   if (flags[n] & FLAG_SOLID) {
@@ -463,6 +467,20 @@ __device__ __forceinline__ void collide_adj(const float (&f)[Q], float phi0,
   o.phi0b = phi0b;
 }
 
+// FP64 sum of one value per thread of a 128-thread block (warp shuffles,
+// then the four warp sums in order); the result is valid in thread 0.
+__device__ __forceinline__ double block128_sum(double v, double* sh4) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) sh4[threadIdx.x >> 5] = v;
+  __syncthreads();
+  return (sh4[0] + sh4[1]) + (sh4[2] + sh4[3]);
+}
+
+// Per fluid node: the collision recomputed from the taped pull and reversed.
+// Block = 128 nodes of one x row (blockIdx.y = y, blockIdx.z = z); the
+// block's dL/dsigma share goes to partial[block].
+template <typename IDX>
 __global__ void __launch_bounds__(128)
 adj_lb_node(const float* __restrict__ fprev, const float* __restrict__ phig,
             const uint8_t* __restrict__ flags, const float* __restrict__ fstarb,
@@ -470,85 +488,91 @@ adj_lb_node(const float* __restrict__ fprev, const float* __restrict__ phig,
             float* __restrict__ finb, float* __restrict__ nodeb,
             double* __restrict__ partial, Grid g, Consts k, float dbeta4_dsigma,
             float dkphi_dsigma) {
-  __shared__ double sh[128];
-  const int64_t n = (int64_t)blockIdx.x * 128 + threadIdx.x;
-  const int64_t N = g.N;
+  __shared__ double sh4[4];
+  const int x = blockIdx.x * 128 + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const IDX N = (IDX)g.N;
+  const IDX nx = g.nx;
+  const IDX nxy = (IDX)g.nx * g.ny;
+  const IDX n = (IDX)x + nx * y + nxy * z;
   double sig = 0.0;
-  if (n < N && !(flags[n] & FLAG_SOLID)) {
-    const int x = (int)(n % g.nx);
-    const int y = (int)((n / g.nx) % g.ny);
-    const int z = (int)(n / ((int64_t)g.nx * g.ny));
-    const int64_t nxy = (int64_t)g.nx * g.ny;
-    const int xo[3] = {wrap(x, -1, g.nx), x, wrap(x, 1, g.nx)};
-    const int yo[3] = {wrap(y, -1, g.ny) * g.nx, y * g.nx, wrap(y, 1, g.ny) * g.nx};
-    const int64_t zo[3] = {wrap(z, -1, g.nz) * nxy, z * nxy, wrap(z, 1, g.nz) * nxy};
+  if (x < g.nx && !(flags[n] & FLAG_SOLID)) {
+    const IDX xo[3] = {(IDX)wrap(x, -1, g.nx), (IDX)x, (IDX)wrap(x, 1, g.nx)};
+    const IDX yo[3] = {wrap(y, -1, g.ny) * nx, y * nx, wrap(y, 1, g.ny) * nx};
+    const IDX zo[3] = {wrap(z, -1, g.nz) * nxy, z * nxy, wrap(z, 1, g.nz) * nxy};
+    const bool near = flags[n] & FLAG_NEAR;
     float f[Q], fob[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const int64_t src = xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)];
-      const bool bb = (q != REST) && (flags[src] & FLAG_SOLID);
-      f[q] = bb ? fprev[(int64_t)opp(q) * N + n] : fprev[(int64_t)q * N + src];
-      fob[q] = fstarb[(int64_t)q * N + n];
+      const IDX src = xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)];
+      const bool bb = near && (q != REST) && (flags[src] & FLAG_SOLID);
+      f[q] = bb ? fprev[opp(q) * N + n] : fprev[q * N + src];
+      fob[q] = fstarb[q * N + n];
     }
-    float gx, gy, gz, ssum;
-    phi_stencil(phig, xo, yo, zo, gx, gy, gz, ssum);
+    float gx = 0.f, gy = 0.f, gz = 0.f, ssum = 0.f;
+#pragma unroll
+    for (int q = 0; q < REST; ++q) {
+      const float vp = __ldg(phig + (xo[1 + cx(q)] + yo[1 + cy(q)] + zo[1 + cz(q)]));
+      const float vm = __ldg(phig + (xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)]));
+      stencil_pair(q, vp, vm, gx, gy, gz, ssum);
+    }
     const float phi0 = phig[n];
     const float lap = 6.0f * (ssum - (1.0f - wq(REST)) * phi0);
     LbAdjOut o;
     collide_adj(f, phi0, gx, gy, gz, lap, k, fob, ub[n], ub[N + n], ub[2 * N + n],
                 acb[n], acb[N + n], acb[2 * N + n], o);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) finb[(int64_t)q * N + n] = o.fb[q];
+    for (int q = 0; q < Q; ++q) finb[q * N + n] = o.fb[q];
     nodeb[n] = o.gbx;
     nodeb[N + n] = o.gby;
     nodeb[2 * N + n] = o.gbz;
     nodeb[3 * N + n] = o.lapb;
     nodeb[4 * N + n] = o.phi0b;
     sig = (double)o.beta4b * dbeta4_dsigma + (double)o.kphib * dkphi_dsigma;
-  } else if (n < N) {
+  } else if (x < g.nx) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) finb[(int64_t)q * N + n] = 0.f;
+    for (int q = 0; q < Q; ++q) finb[q * N + n] = 0.f;
 #pragma unroll
     for (int c = 0; c < 5; ++c) nodeb[c * N + n] = 0.f;
   }
-  sh[threadIdx.x] = sig;
-  __syncthreads();
-  for (int w = 64; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+  const double tot = block128_sum(sig, sh4);
+  if (threadIdx.x == 0)
+    partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
 }
 
 // Transpose of the pull (populations) and of the phi stencil (gradient,
-// Laplacian, own value), gathered per node.
+// Laplacian, own value), gathered per node; same launch shape as
+// adj_lb_node.
+template <typename IDX>
 __global__ void __launch_bounds__(128)
 adj_lb_gather(const uint8_t* __restrict__ flags, const float* __restrict__ finb,
               const float* __restrict__ nodeb, float* __restrict__ fprevb,
               float* __restrict__ phigb, Grid g) {
-  const int64_t n = (int64_t)blockIdx.x * 128 + threadIdx.x;
-  const int64_t N = g.N;
-  if (n >= N) return;
-  const int x = (int)(n % g.nx);
-  const int y = (int)((n / g.nx) % g.ny);
-  const int z = (int)(n / ((int64_t)g.nx * g.ny));
-  const int64_t nxy = (int64_t)g.nx * g.ny;
-  const int xo[3] = {wrap(x, -1, g.nx), x, wrap(x, 1, g.nx)};
-  const int64_t yo[3] = {(int64_t)wrap(y, -1, g.ny) * g.nx, (int64_t)y * g.nx,
-                         (int64_t)wrap(y, 1, g.ny) * g.nx};
-  const int64_t zo[3] = {wrap(z, -1, g.nz) * nxy, z * nxy, wrap(z, 1, g.nz) * nxy};
-  const bool solid = flags[n] & FLAG_SOLID;
+  const int x = blockIdx.x * 128 + threadIdx.x;
+  if (x >= g.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const IDX N = (IDX)g.N;
+  const IDX nx = g.nx;
+  const IDX nxy = (IDX)g.nx * g.ny;
+  const IDX n = (IDX)x + nx * y + nxy * z;
+  const IDX xo[3] = {(IDX)wrap(x, -1, g.nx), (IDX)x, (IDX)wrap(x, 1, g.nx)};
+  const IDX yo[3] = {wrap(y, -1, g.ny) * nx, y * nx, wrap(y, 1, g.ny) * nx};
+  const IDX zo[3] = {wrap(z, -1, g.nz) * nxy, z * nxy, wrap(z, 1, g.nz) * nxy};
+  const uint8_t fl = flags[n];
+  const bool solid = fl & FLAG_SOLID;
+  const bool near = fl & FLAG_NEAR;
   // populations: f_prev[q](y) fed f_in[q](y + c_q), or f_in[opp q](y) when
-  // y + c_q is solid (halfway bounce-back)
+  // y + c_q is solid (halfway bounce-back; only nodes flagged near have a
+  // solid neighbour)
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     float v = 0.f;
     if (!solid) {
-      const int64_t dst = xo[1 + cx(q)] + yo[1 + cy(q)] + zo[1 + cz(q)];
-      v = (q != REST && (flags[dst] & FLAG_SOLID)) ? finb[(int64_t)opp(q) * N + n]
-                                                    : finb[(int64_t)q * N + dst];
+      const IDX dst = xo[1 + cx(q)] + yo[1 + cy(q)] + zo[1 + cz(q)];
+      v = (near && q != REST && (flags[dst] & FLAG_SOLID)) ? finb[opp(q) * N + n]
+                                                           : finb[q * N + dst];
     }
-    fprevb[(int64_t)q * N + n] = v;
+    fprevb[q * N + n] = v;
   }
   // phi at y entered grad_iso and lap_iso of every fluid x = y - c_i, and
   // phi0 of x = y
@@ -557,7 +581,7 @@ adj_lb_gather(const uint8_t* __restrict__ flags, const float* __restrict__ finb,
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     if (q == REST) continue;
-    const int64_t m = xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)];  // y - c_q
+    const IDX m = xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)];  // y - c_q
     acc += 3.f * wq(q) *
            (cx(q) * nodeb[m] + cy(q) * nodeb[N + m] + cz(q) * nodeb[2 * N + m]);
     lsum += wq(q) * nodeb[3 * N + m];
@@ -676,6 +700,7 @@ struct AdjointState {
         *phigb = nullptr, *ub = nullptr, *ab = nullptr, *face = nullptr,
         *finb = nullptr, *nodeb = nullptr, *wd = nullptr;
   double *thetab = nullptr, *sigmab = nullptr, *partial = nullptr;
+  float* scal = nullptr;  // S / W and lambda of the correction adjoint
   int npart = 0;
   int32_t *row_start = nullptr, *row_entry = nullptr;
   bool forward_done = false;
@@ -689,7 +714,7 @@ void adjoint_free(AdjointState* s) {
     for (float* p : *v) cudaFree(p);
   void* bufs[] = {s->ck_mass, s->t_mass, s->fb, s->fb2, s->phib, s->phisb, s->phigb, s->ub,
                   s->ab, s->face, s->finb, s->nodeb, s->wd, s->thetab, s->sigmab,
-                  s->partial, s->row_start, s->row_entry};
+                  s->partial, s->scal, s->row_start, s->row_entry};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete s;
@@ -751,39 +776,34 @@ cacl_status build_transpose(cacl_ctx* c, AdjointState* s) {
   return CACL_OK;
 }
 
-// One forward step through the parts, recording the tape slot t if >= 0.
-cacl_status taped_step(cacl_ctx* c, AdjointState* s, int t) {
+// Step t of a segment's recompute, recording tape slot t. The populations
+// need no copy: the step reads f*^{n-1} from slot t (the checkpoint was
+// restored into slot 0) and the collide-stream writes f*^n straight into
+// slot t + 1 (the context's spare buffer after the last step).
+cacl_status taped_step(cacl_ctx* c, AdjointState* s, int t, int len) {
   const int64_t N = c->g.N;
-  const size_t fb = sizeof(float) * Q * N, pb = sizeof(float) * N;
-  if (t >= 0) {
-    ACK(cudaMemcpyAsync(s->t_fprev[t], c->f[c->fcur], fb, cudaMemcpyDeviceToDevice,
-                        c->stream), "tape");
-    ACK(cudaMemcpyAsync(s->t_phipre[t], c->phi[c->pcur], pb,
-                        cudaMemcpyDeviceToDevice, c->stream), "tape");
-  }
+  const size_t pb = sizeof(float) * N;
+  ACK(cudaMemcpyAsync(s->t_phipre[t], c->phi[c->pcur], pb, cudaMemcpyDeviceToDevice,
+                      c->stream), "tape");
   cacl_status st = cacl_ghost_update(c);
   if (st != CACL_OK) return st;
-  if (t >= 0)
-    ACK(cudaMemcpyAsync(s->t_phig[t], c->phi[c->pcur], pb, cudaMemcpyDeviceToDevice,
-                        c->stream), "tape");
-  if ((st = cacl_lb_collide(c)) != CACL_OK) return st;
-  if (t >= 0) {
-    ACK(cudaMemcpyAsync(s->t_u[t], c->u, 3 * pb, cudaMemcpyDeviceToDevice, c->stream),
-        "tape");
-    ACK(cudaMemcpyAsync(s->t_a[t], c->a, 3 * pb, cudaMemcpyDeviceToDevice, c->stream),
-        "tape");
-  }
+  ACK(cudaMemcpyAsync(s->t_phig[t], c->phi[c->pcur], pb, cudaMemcpyDeviceToDevice,
+                      c->stream), "tape");
+  float* fout = (t + 1 < len) ? s->t_fprev[t + 1] : (float*)c->f[1 - c->fcur];
+  ACK(launch_lb(c, s->t_fprev[t], fout, c->phi[c->pcur]), "collide-stream");
+  ACK(cudaMemcpyAsync(s->t_u[t], c->u, 3 * pb, cudaMemcpyDeviceToDevice, c->stream),
+      "tape");
+  ACK(cudaMemcpyAsync(s->t_a[t], c->a, 3 * pb, cudaMemcpyDeviceToDevice, c->stream),
+      "tape");
   // the phi update of a full step reads the compressive vector the
   // collide-stream just wrote (launch_phase, not the part entry point)
   ACK(launch_phase(c, c->phi[c->pcur], c->phi[1 - c->pcur]), "phase");
   c->pcur ^= 1;
-  if (t >= 0)
-    ACK(cudaMemcpyAsync(s->t_phis[t], c->phi[c->pcur], pb, cudaMemcpyDeviceToDevice,
-                        c->stream), "tape");
+  ACK(cudaMemcpyAsync(s->t_phis[t], c->phi[c->pcur], pb, cudaMemcpyDeviceToDevice,
+                      c->stream), "tape");
   if ((st = cacl_volume_correct(c)) != CACL_OK) return st;
-  if (t >= 0)
-    ACK(cudaMemcpyAsync(s->t_mass + t, c->mass, sizeof(MassScalars),
-                        cudaMemcpyDeviceToDevice, c->stream), "tape");
+  ACK(cudaMemcpyAsync(s->t_mass + t, c->mass, sizeof(MassScalars),
+                      cudaMemcpyDeviceToDevice, c->stream), "tape");
   return CACL_OK;
 }
 
@@ -843,8 +863,9 @@ cacl_status cacl_adjoint_forward(cacl_ctx* c, int nsteps, int every) {
     ACK(alloc(&s->wd, (size_t)Q * (s->W > 0 ? s->W : 1)), "alloc adjoint");
     ACK(alloc(&s->thetab, s->W > 0 ? s->W : 1), "alloc adjoint");
     ACK(alloc(&s->sigmab, 1), "alloc adjoint");
-    s->npart = std::max(nblk(N, 128), 1024);
+    s->npart = std::max((int)(((c->g.nx + 127) / 128) * (int64_t)c->g.ny * c->g.nz), 1024);
     ACK(alloc(&s->partial, s->npart), "alloc adjoint");
+    ACK(alloc(&s->scal, 2), "alloc adjoint");
     const cacl_status st = build_transpose(c, s);
     if (st != CACL_OK) return st;
   }
@@ -901,18 +922,19 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
   ACK(cudaMemsetAsync(s->sigmab, 0, sizeof(double), st), "seed");
 
   const int nseg = (s->nsteps + s->every - 1) / s->every;
+  const bool small = (int64_t)Q * N < (int64_t)INT32_MAX;  // 32-bit offsets
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int n0 = seg * s->every;
     const int len = std::min(s->every, s->nsteps - n0);
     // recompute the segment with its tape
-    ACK(cudaMemcpyAsync(c->f[c->fcur], s->ck_f[seg], sizeof(float) * Q * N,
+    ACK(cudaMemcpyAsync(s->t_fprev[0], s->ck_f[seg], sizeof(float) * Q * N,
                         cudaMemcpyDeviceToDevice, st), "restore");
     ACK(cudaMemcpyAsync(c->phi[c->pcur], s->ck_phi[seg], sizeof(float) * N,
                         cudaMemcpyDeviceToDevice, st), "restore");
     ACK(cudaMemcpyAsync(c->mass, s->ck_mass + seg, sizeof(MassScalars),
                         cudaMemcpyDeviceToDevice, st), "restore");
     for (int t = 0; t < len; ++t) {
-      const cacl_status r = taped_step(c, s, t);
+      const cacl_status r = taped_step(c, s, t, len);
       if (r != CACL_OK) return r;
     }
     for (int t = len - 1; t >= 0; --t) {
@@ -920,22 +942,33 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
       const int nb_sum = std::min(nblk(N, AT), 1024);
       adj_correct_sum<<<nb_sum, AT, 0, st>>>(s->phib, s->t_phis[t], c->flags, N, eps,
                                              s->partial);
+      adj_correct_scalars<<<1, 32, 0, st>>>(s->partial, nb_sum, s->t_mass + t, s->scal);
       adj_correct_apply<<<nblk(N, AT), AT, 0, st>>>(s->phib, s->t_phis[t], c->flags,
-                                                    N, eps, s->partial, nb_sum,
-                                                    s->t_mass + t, s->phisb);
+                                                    N, eps, s->scal, s->phisb);
       // A2 phi update
       adj_phase_faces<<<nblk(N, AT), AT, 0, st>>>(s->t_phig[t], s->t_u[t], c->flags,
                                                   s->phisb, s->face, g);
       adj_phase_gather<<<nblk(N, AT), AT, 0, st>>>(c->flags, s->phisb, s->face,
                                                    s->phigb, s->ub, s->ab, g, c->k);
       // A3 collide-stream
-      const int nbl = nblk(N, 128);
-      adj_lb_node<<<nbl, 128, 0, st>>>(s->t_fprev[t], s->t_phig[t], c->flags, s->fb,
-                                       s->ub, s->ab, s->finb, s->nodeb, s->partial,
-                                       g, c->k, db4, dkp);
+      const dim3 rows((g.nx + 127) / 128, g.ny, g.nz);
+      const int nbl = (int)(rows.x * rows.y * rows.z);
+      if (small) {
+        adj_lb_node<int><<<rows, 128, 0, st>>>(s->t_fprev[t], s->t_phig[t], c->flags,
+                                               s->fb, s->ub, s->ab, s->finb, s->nodeb,
+                                               s->partial, g, c->k, db4, dkp);
+      } else {
+        adj_lb_node<int64_t><<<rows, 128, 0, st>>>(
+            s->t_fprev[t], s->t_phig[t], c->flags, s->fb, s->ub, s->ab, s->finb,
+            s->nodeb, s->partial, g, c->k, db4, dkp);
+      }
       sum_partials<<<1, 128, 0, st>>>(s->partial, nbl, s->sigmab);
-      adj_lb_gather<<<nbl, 128, 0, st>>>(c->flags, s->finb, s->nodeb, s->fb2,
-                                         s->phigb, g);
+      if (small)
+        adj_lb_gather<int><<<rows, 128, 0, st>>>(c->flags, s->finb, s->nodeb, s->fb2,
+                                                 s->phigb, g);
+      else
+        adj_lb_gather<int64_t><<<rows, 128, 0, st>>>(c->flags, s->finb, s->nodeb,
+                                                     s->fb2, s->phigb, g);
       std::swap(s->fb, s->fb2);
       // A4 ghost map
       if (W > 0)
