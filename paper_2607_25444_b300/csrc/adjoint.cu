@@ -110,31 +110,56 @@ __device__ __forceinline__ float minmod_v(float a, float b) {
 // Per node l and axis d: adjoints of the face flux between l and l + e_d,
 // written as contributions to phi at l-1, l, l+1, l+2 and to u_d at l and
 // l + 1 (equal halves).
-__global__ void __launch_bounds__(AT)
+// Node (x, y, z) of a row-shaped launch (128 threads along x, blockIdx.y =
+// y, blockIdx.z = z) and the offsets of its neighbours at -2 .. +2 along
+// each axis (periodic wrap, any extent >= 1).
+template <typename IDX>
+struct RowNode {
+  int x, y, z;
+  IDX n;
+  IDX d[3][5];  // d[axis][s + 2]: offset of the node s cells along the axis
+  __device__ __forceinline__ bool init(const Grid& g) {
+    x = blockIdx.x * 128 + threadIdx.x;
+    y = blockIdx.y;
+    z = blockIdx.z;
+    if (x >= g.nx) return false;
+    const IDX nx = g.nx, nxy = (IDX)g.nx * g.ny;
+    n = (IDX)x + nx * y + nxy * z;
+    const int c[3] = {x, y, z}, e[3] = {g.nx, g.ny, g.nz};
+    const IDX st[3] = {1, nx, nxy};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int s = -2; s <= 2; ++s) {
+        int j = c[a] + s;
+        if (j < 0) j += e[a];
+        if (j < 0) j += e[a];
+        if (j >= e[a]) j -= e[a];
+        if (j >= e[a]) j -= e[a];
+        d[a][s + 2] = (IDX)(j - c[a]) * st[a];
+      }
+    return true;
+  }
+};
+
+template <typename IDX>
+__global__ void __launch_bounds__(128)
 adj_phase_faces(const float* __restrict__ phi, const float* __restrict__ u,
                 const uint8_t* __restrict__ flags,
                 const float* __restrict__ phisb, float* __restrict__ face,
                 Grid g) {
-  const int64_t n = (int64_t)blockIdx.x * AT + threadIdx.x;
-  if (n >= g.N) return;
-  const int x = (int)(n % g.nx);
-  const int y = (int)((n / g.nx) % g.ny);
-  const int z = (int)(n / ((int64_t)g.nx * g.ny));
-  const int64_t nxy = (int64_t)g.nx * g.ny;
-  const int64_t N = g.N;
+  RowNode<IDX> rn;
+  if (!rn.init(g)) return;
+  const IDX n = rn.n;
+  const IDX N = (IDX)g.N;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    auto at = [&](int s) -> int64_t {
-      const int xx = d == 0 ? (int)(((int64_t)x + s + 4LL * g.nx) % g.nx) : x;
-      const int yy = d == 1 ? (int)(((int64_t)y + s + 4LL * g.ny) % g.ny) : y;
-      const int zz = d == 2 ? (int)(((int64_t)z + s + 4LL * g.nz) % g.nz) : z;
-      return xx + (int64_t)g.nx * yy + nxy * zz;
-    };
-    float* fc = face + (int64_t)d * 5 * N;
+    auto at = [&](int s) -> IDX { return n + rn.d[d][s + 2]; };
+    float* fc = face + (IDX)d * 5 * N;
     float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f, cu = 0.f;
-    const int64_t l = n, r = at(1);
+    const IDX l = n, r = at(1);
     if (!(flags[l] & FLAG_SOLID) && !(flags[r] & FLAG_SOLID)) {
-      const int64_t lm = at(-1), rp = at(2);
+      const IDX lm = at(-1), rp = at(2);
       const float pm = phi[lm], pl = phi[l], pr = phi[r], pp = phi[rp];
       const float fb = phisb[r] - phisb[l];  // d L / d F(l, r)
       const float uf = 0.5f * (u[d * N + l] + u[d * N + r]);
@@ -168,28 +193,22 @@ adj_phase_faces(const float* __restrict__ phi, const float* __restrict__ u,
   }
 }
 
-__global__ void __launch_bounds__(AT)
+template <typename IDX>
+__global__ void __launch_bounds__(128)
 adj_phase_gather(const uint8_t* __restrict__ flags,
                  const float* __restrict__ phisb, const float* __restrict__ face,
                  float* __restrict__ phigb, float* __restrict__ ub,
                  float* __restrict__ ab, Grid g, Consts k) {
-  const int64_t n = (int64_t)blockIdx.x * AT + threadIdx.x;
-  if (n >= g.N) return;
-  const int x = (int)(n % g.nx);
-  const int y = (int)((n / g.nx) % g.ny);
-  const int z = (int)(n / ((int64_t)g.nx * g.ny));
-  const int64_t nxy = (int64_t)g.nx * g.ny;
-  const int64_t N = g.N;
-  const int xo[3] = {wrap(x, -1, g.nx), x, wrap(x, 1, g.nx)};
-  const int64_t yo[3] = {(int64_t)wrap(y, -1, g.ny) * g.nx, (int64_t)y * g.nx,
-                         (int64_t)wrap(y, 1, g.ny) * g.nx};
-  const int64_t zo[3] = {wrap(z, -1, g.nz) * nxy, z * nxy, wrap(z, 1, g.nz) * nxy};
+  RowNode<IDX> rn;
+  if (!rn.init(g)) return;
+  const IDX n = rn.n;
+  const IDX N = (IDX)g.N;
   // fluid-masked phi*_bar at the 27 neighbours: lap_iso and grad_iso of it
   float lsum = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     if (q == REST) continue;
-    const int64_t m = xo[1 + cx(q)] + yo[1 + cy(q)] + zo[1 + cz(q)];
+    const IDX m = n + rn.d[0][2 + cx(q)] + rn.d[1][2 + cy(q)] + rn.d[2][2 + cz(q)];
     const float v = (flags[m] & FLAG_SOLID) ? 0.f : phisb[m];
     lsum += wq(q) * v;
     gx += 3.f * wq(q) * cx(q) * v;
@@ -202,13 +221,8 @@ adj_phase_gather(const uint8_t* __restrict__ flags,
   // face flux contributions along each axis
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    auto at = [&](int s) -> int64_t {
-      const int xx = d == 0 ? (int)(((int64_t)x + s + 4LL * g.nx) % g.nx) : x;
-      const int yy = d == 1 ? (int)(((int64_t)y + s + 4LL * g.ny) % g.ny) : y;
-      const int zz = d == 2 ? (int)(((int64_t)z + s + 4LL * g.nz) % g.nz) : z;
-      return xx + (int64_t)g.nx * yy + nxy * zz;
-    };
-    const float* fc = face + (int64_t)d * 5 * N;
+    auto at = [&](int s) -> IDX { return n + rn.d[d][s + 2]; };
+    const float* fc = face + (IDX)d * 5 * N;
     // node n is position l-1 of face (n+1), l of face n, l+1 of face (n-1),
     // l+2 of face (n-2)
     acc += fc[at(1)] + fc[N + n] + fc[2 * N + at(-1)] + fc[3 * N + at(-2)];
@@ -480,10 +494,15 @@ __device__ __forceinline__ double block128_sum(double v, double* sh4) {
 // Per fluid node: the collision recomputed from the taped pull and reversed.
 // Block = 128 nodes of one x row (blockIdx.y = y, blockIdx.z = z); the
 // block's dL/dsigma share goes to partial[block].
+// The adjoint of the node's post-collision populations f*_q(n) is gathered
+// from the pulled-population adjoints of the later step (finb_later, or
+// zero when null) through the transpose of the pull: f*_q(n) fed
+// f_in[q](n + c_q), or f_in[opp q](n) when n + c_q is solid (halfway
+// bounce-back; only nodes flagged near have a solid neighbour).
 template <typename IDX>
 __global__ void __launch_bounds__(128)
 adj_lb_node(const float* __restrict__ fprev, const float* __restrict__ phig,
-            const uint8_t* __restrict__ flags, const float* __restrict__ fstarb,
+            const uint8_t* __restrict__ flags, const float* __restrict__ finb_later,
             const float* __restrict__ ub, const float* __restrict__ acb,
             float* __restrict__ finb, float* __restrict__ nodeb,
             double* __restrict__ partial, Grid g, Consts k, float dbeta4_dsigma,
@@ -507,7 +526,13 @@ adj_lb_node(const float* __restrict__ fprev, const float* __restrict__ phig,
       const IDX src = xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)];
       const bool bb = near && (q != REST) && (flags[src] & FLAG_SOLID);
       f[q] = bb ? fprev[opp(q) * N + n] : fprev[q * N + src];
-      fob[q] = fstarb[q * N + n];
+      if (finb_later) {
+        const IDX dst = xo[1 + cx(q)] + yo[1 + cy(q)] + zo[1 + cz(q)];
+        const bool bt = near && (q != REST) && (flags[dst] & FLAG_SOLID);
+        fob[q] = bt ? finb_later[opp(q) * N + n] : finb_later[q * N + dst];
+      } else {
+        fob[q] = 0.f;
+      }
     }
     float gx = 0.f, gy = 0.f, gz = 0.f, ssum = 0.f;
 #pragma unroll
@@ -540,14 +565,11 @@ adj_lb_node(const float* __restrict__ fprev, const float* __restrict__ phig,
     partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
 }
 
-// Transpose of the pull (populations) and of the phi stencil (gradient,
-// Laplacian, own value), gathered per node; same launch shape as
-// adj_lb_node.
+// Transpose of the phi stencil (gradient, Laplacian, own value) of the
+// collide-stream, gathered per node; same launch shape as adj_lb_node.
 template <typename IDX>
 __global__ void __launch_bounds__(128)
-adj_lb_gather(const uint8_t* __restrict__ flags, const float* __restrict__ finb,
-              const float* __restrict__ nodeb, float* __restrict__ fprevb,
-              float* __restrict__ phigb, Grid g) {
+adj_lb_gather(const float* __restrict__ nodeb, float* __restrict__ phigb, Grid g) {
   const int x = blockIdx.x * 128 + threadIdx.x;
   if (x >= g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
@@ -558,22 +580,6 @@ adj_lb_gather(const uint8_t* __restrict__ flags, const float* __restrict__ finb,
   const IDX xo[3] = {(IDX)wrap(x, -1, g.nx), (IDX)x, (IDX)wrap(x, 1, g.nx)};
   const IDX yo[3] = {wrap(y, -1, g.ny) * nx, y * nx, wrap(y, 1, g.ny) * nx};
   const IDX zo[3] = {wrap(z, -1, g.nz) * nxy, z * nxy, wrap(z, 1, g.nz) * nxy};
-  const uint8_t fl = flags[n];
-  const bool solid = fl & FLAG_SOLID;
-  const bool near = fl & FLAG_NEAR;
-  // populations: f_prev[q](y) fed f_in[q](y + c_q), or f_in[opp q](y) when
-  // y + c_q is solid (halfway bounce-back; only nodes flagged near have a
-  // solid neighbour)
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    float v = 0.f;
-    if (!solid) {
-      const IDX dst = xo[1 + cx(q)] + yo[1 + cy(q)] + zo[1 + cz(q)];
-      v = (near && q != REST && (flags[dst] & FLAG_SOLID)) ? finb[opp(q) * N + n]
-                                                           : finb[q * N + dst];
-    }
-    fprevb[q * N + n] = v;
-  }
   // phi at y entered grad_iso and lap_iso of every fluid x = y - c_i, and
   // phi0 of x = y
   float acc = nodeb[4 * N + n];
@@ -696,9 +702,11 @@ struct AdjointState {
   std::vector<float*> t_fprev, t_phipre, t_phig, t_u, t_a, t_phis;
   MassScalars* t_mass = nullptr;  // [every]
   // adjoint fields
+  // fb / fb2: adjoints of the pulled populations f_in of a step and of the
+  // step before (ping-pong)
   float *fb = nullptr, *fb2 = nullptr, *phib = nullptr, *phisb = nullptr,
         *phigb = nullptr, *ub = nullptr, *ab = nullptr, *face = nullptr,
-        *finb = nullptr, *nodeb = nullptr, *wd = nullptr;
+        *nodeb = nullptr, *wd = nullptr;
   double *thetab = nullptr, *sigmab = nullptr, *partial = nullptr;
   float* scal = nullptr;  // S / W and lambda of the correction adjoint
   int npart = 0;
@@ -713,7 +721,7 @@ void adjoint_free(AdjointState* s) {
                   &s->t_u, &s->t_a, &s->t_phis})
     for (float* p : *v) cudaFree(p);
   void* bufs[] = {s->ck_mass, s->t_mass, s->fb, s->fb2, s->phib, s->phisb, s->phigb, s->ub,
-                  s->ab, s->face, s->finb, s->nodeb, s->wd, s->thetab, s->sigmab,
+                  s->ab, s->face, s->nodeb, s->wd, s->thetab, s->sigmab,
                   s->partial, s->scal, s->row_start, s->row_entry};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -852,7 +860,6 @@ cacl_status cacl_adjoint_forward(cacl_ctx* c, int nsteps, int every) {
     ACK(alloc(&s->ck_mass, nck), "alloc checkpoint");
     ACK(alloc(&s->fb, (size_t)Q * N), "alloc adjoint");
     ACK(alloc(&s->fb2, (size_t)Q * N), "alloc adjoint");
-    ACK(alloc(&s->finb, (size_t)Q * N), "alloc adjoint");
     ACK(alloc(&s->phib, N), "alloc adjoint");
     ACK(alloc(&s->phisb, N), "alloc adjoint");
     ACK(alloc(&s->phigb, N), "alloc adjoint");
@@ -917,12 +924,13 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
 
   ACK(cudaMemcpyAsync(s->phib, dL_dphi, sizeof(float) * N, cudaMemcpyDeviceToDevice, st),
       "seed");
-  ACK(cudaMemsetAsync(s->fb, 0, sizeof(float) * Q * N, st), "seed");
   ACK(cudaMemsetAsync(s->thetab, 0, sizeof(double) * (W > 0 ? W : 1), st), "seed");
   ACK(cudaMemsetAsync(s->sigmab, 0, sizeof(double), st), "seed");
 
   const int nseg = (s->nsteps + s->every - 1) / s->every;
   const bool small = (int64_t)Q * N < (int64_t)INT32_MAX;  // 32-bit offsets
+  const bool small15 = (int64_t)15 * N < (int64_t)INT32_MAX;  // face buffer
+  bool first = true;  // no later step: dL/df* of the final populations is 0
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int n0 = seg * s->every;
     const int len = std::min(s->every, s->nsteps - n0);
@@ -946,30 +954,39 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
       adj_correct_apply<<<nblk(N, AT), AT, 0, st>>>(s->phib, s->t_phis[t], c->flags,
                                                     N, eps, s->scal, s->phisb);
       // A2 phi update
-      adj_phase_faces<<<nblk(N, AT), AT, 0, st>>>(s->t_phig[t], s->t_u[t], c->flags,
-                                                  s->phisb, s->face, g);
-      adj_phase_gather<<<nblk(N, AT), AT, 0, st>>>(c->flags, s->phisb, s->face,
-                                                   s->phigb, s->ub, s->ab, g, c->k);
-      // A3 collide-stream
       const dim3 rows((g.nx + 127) / 128, g.ny, g.nz);
+      if (small15) {
+        adj_phase_faces<int><<<rows, 128, 0, st>>>(s->t_phig[t], s->t_u[t], c->flags,
+                                                   s->phisb, s->face, g);
+        adj_phase_gather<int><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face,
+                                                    s->phigb, s->ub, s->ab, g, c->k);
+      } else {
+        adj_phase_faces<int64_t><<<rows, 128, 0, st>>>(s->t_phig[t], s->t_u[t],
+                                                       c->flags, s->phisb, s->face, g);
+        adj_phase_gather<int64_t><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face,
+                                                        s->phigb, s->ub, s->ab, g,
+                                                        c->k);
+      }
+      // A3 collide-stream
       const int nbl = (int)(rows.x * rows.y * rows.z);
+      // the later step's pulled-population adjoints (none after the last)
+      const float* later = first ? nullptr : s->fb;
       if (small) {
         adj_lb_node<int><<<rows, 128, 0, st>>>(s->t_fprev[t], s->t_phig[t], c->flags,
-                                               s->fb, s->ub, s->ab, s->finb, s->nodeb,
+                                               later, s->ub, s->ab, s->fb2, s->nodeb,
                                                s->partial, g, c->k, db4, dkp);
       } else {
         adj_lb_node<int64_t><<<rows, 128, 0, st>>>(
-            s->t_fprev[t], s->t_phig[t], c->flags, s->fb, s->ub, s->ab, s->finb,
+            s->t_fprev[t], s->t_phig[t], c->flags, later, s->ub, s->ab, s->fb2,
             s->nodeb, s->partial, g, c->k, db4, dkp);
       }
+      std::swap(s->fb, s->fb2);  // fb: this step's pulled-population adjoints
+      first = false;
       sum_partials<<<1, 128, 0, st>>>(s->partial, nbl, s->sigmab);
       if (small)
-        adj_lb_gather<int><<<rows, 128, 0, st>>>(c->flags, s->finb, s->nodeb, s->fb2,
-                                                 s->phigb, g);
+        adj_lb_gather<int><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
       else
-        adj_lb_gather<int64_t><<<rows, 128, 0, st>>>(c->flags, s->finb, s->nodeb,
-                                                     s->fb2, s->phigb, g);
-      std::swap(s->fb, s->fb2);
+        adj_lb_gather<int64_t><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
       // A4 ghost map
       if (W > 0)
         adj_ghost_node<<<nblk(W, 128), 128, 0, st>>>(
