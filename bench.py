@@ -315,7 +315,7 @@ def run_adjoint(args, torch, cacl, stream):
     x, y = idx % n, (idx // n) % n
     patches = I.SplitMix64(7).array(64, 45.0, 135.0)
     theta_w = patches[(y // 12) * 8 + (x // 12)].astype(np.float32)
-    steps, every = 200, 50
+    steps, every = args.adjoint_steps, args.adjoint_every
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     s.set_fields(phi)
     s.set_wall_angles(theta_w)
@@ -570,11 +570,27 @@ def main():
                     default=[30.0, 60.0, 90.0, 120.0, 150.0])
     ap.add_argument("--checkpoints", type=int, nargs="*",
                     default=[10000, 20000, 30000, 40000])
+    ap.add_argument("--adjoint-steps", type=int, default=200,
+                    help="rollout length of the adjoint/forward cost measurement")
+    ap.add_argument("--adjoint-every", type=int, default=50,
+                    help="checkpoint interval of that measurement")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint/forward cost measurement and "
+                         "print its JSON (for profiling the adjoint kernels)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.theta_recovery:
         run_theta_recovery(args)
+        return
+    if args.adjoint_only:
+        import torch
+
+        from paper_2607_25444_b300 import cacl
+        torch.cuda.set_device(0)
+        torch.cuda.set_stream(torch.cuda.Stream())
+        print(json.dumps(run_adjoint(args, torch, cacl, torch.cuda.current_stream())),
+              flush=True)
         return
     if args.impl == "reference":
         run_reference(args)
