@@ -204,6 +204,20 @@ cacl_status cacl_adjoint_forward(cacl_ctx* ctx, int nsteps, int ckpt_every);
 cacl_status cacl_adjoint_backward(cacl_ctx* ctx, const float* dL_dphi,
                                   double* dL_dtheta, double* dL_dsigma);
 
+/* Two-level checkpointing for long rollouts: as cacl_adjoint_forward, but
+ * the forward keeps a checkpoint only every outer_every steps (a positive
+ * multiple of ckpt_every; 0 = one level, the same as cacl_adjoint_forward).
+ * cacl_adjoint_backward then recomputes each outer segment once from its
+ * checkpoint to rebuild the checkpoints every ckpt_every steps inside it,
+ * and proceeds as with one level; the gradients are bit-identical to the
+ * one-level ones. Device memory: ceil(nsteps / outer_every) + outer_every /
+ * ckpt_every checkpoints of 28 N floats, plus the tape of ckpt_every steps
+ * (36 N floats each), instead of ceil(nsteps / ckpt_every) checkpoints;
+ * every step is computed once more. Returns CACL_ERR_ARG when outer_every
+ * is not a multiple of ckpt_every. */
+cacl_status cacl_adjoint_forward_levels(cacl_ctx* ctx, int nsteps,
+                                        int ckpt_every, int outer_every);
+
 /*
  * Batches: many cases of uneven grid size advanced together (each stage of
  * the step is one grid-strided launch over a work-list spanning all cases,

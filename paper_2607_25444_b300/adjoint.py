@@ -2,7 +2,9 @@
 
 The forward runs nsteps steps of the CUDA path from a fixed initial state
 with the given contact angle of every wall node (degrees, wall-list order)
-and surface tension, keeping checkpoints every ckpt_every steps; the
+and surface tension, keeping checkpoints every ckpt_every steps (or, with
+outer_every > 0, two-level checkpoints: every outer_every steps, rebuilt
+every ckpt_every steps inside each outer segment by the backward); the
 backward runs the library's hand-written adjoint and returns dL/dtheta
 (FP64-accumulated, per wall node) and dL/dsigma. All arithmetic runs in the
 library's kernels; this module only moves tensors across the C ABI.
@@ -13,11 +15,11 @@ import torch
 class Rollout(torch.autograd.Function):
     @staticmethod
     def forward(ctx, theta_wall, sigma, solver, init_phi, init_u, nsteps,
-                ckpt_every):
+                ckpt_every, outer_every=0):
         solver.set_sigma(float(sigma))
         solver.set_fields(init_phi, init_u)
         solver.set_wall_angles(theta_wall.detach().to("cpu", torch.float32).numpy())
-        solver.adjoint_forward(int(nsteps), int(ckpt_every))
+        solver.adjoint_forward(int(nsteps), int(ckpt_every), int(outer_every))
         phi = torch.empty(solver.N, dtype=torch.float32, device="cuda")
         solver.fields_device(phi=phi)
         ctx.solver = solver
@@ -39,11 +41,11 @@ class Rollout(torch.autograd.Function):
         torch.cuda.current_stream().synchronize()
         dth = dth[:ctx.theta_shape[0]].to(ctx.theta_device, ctx.theta_dtype)
         dsg = dsg[0].to(ctx.sigma_device, ctx.sigma_dtype)
-        return dth, dsg, None, None, None, None, None
+        return dth, dsg, None, None, None, None, None, None
 
 
 def rollout(theta_wall, sigma, solver, init_phi, init_u=None, nsteps=100,
-            ckpt_every=10):
+            ckpt_every=10, outer_every=0):
     """phi after nsteps steps; differentiable in theta_wall and sigma."""
     return Rollout.apply(theta_wall, sigma, solver, init_phi, init_u, nsteps,
-                         ckpt_every)
+                         ckpt_every, outer_every)

@@ -31,7 +31,7 @@ EXPORTS = (
     "cacl_batch_create", "cacl_batch_destroy", "cacl_batch_last_error",
     "cacl_batch_case", "cacl_batch_step", "cacl_batch_set_option",
     "cacl_batch_autotune", "cacl_set_wall_angles", "cacl_set_sigma",
-    "cacl_adjoint_forward", "cacl_adjoint_backward",
+    "cacl_adjoint_forward", "cacl_adjoint_forward_levels", "cacl_adjoint_backward",
 )
 OPT_PHASE_TILE = 1
 OPT_PHASE_PIPE = 2  # 0 auto, 1 register staging, 2 asynchronous copies
@@ -111,6 +111,7 @@ def load():
     L.cacl_set_wall_angles.argtypes = [vp, vp]
     L.cacl_set_sigma.argtypes = [vp, C.c_double]
     L.cacl_adjoint_forward.argtypes = [vp, C.c_int, C.c_int]
+    L.cacl_adjoint_forward_levels.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     L.cacl_adjoint_backward.argtypes = [vp, vp, vp, vp]
     for name in EXPORTS:
         f = getattr(L, name)
@@ -323,8 +324,15 @@ class Solver:
     def set_sigma(self, sigma):
         self._check(self.L.cacl_set_sigma(self.h, float(sigma)))
 
-    def adjoint_forward(self, nsteps, ckpt_every):
-        self._check(self.L.cacl_adjoint_forward(self.h, int(nsteps), int(ckpt_every)))
+    def adjoint_forward(self, nsteps, ckpt_every, outer_every=0):
+        """Forward rollout keeping checkpoints for the adjoint; outer_every > 0
+        (a multiple of ckpt_every) selects two-level checkpointing."""
+        if outer_every:
+            self._check(self.L.cacl_adjoint_forward_levels(
+                self.h, int(nsteps), int(ckpt_every), int(outer_every)))
+        else:
+            self._check(self.L.cacl_adjoint_forward(self.h, int(nsteps),
+                                                    int(ckpt_every)))
 
     def adjoint_backward(self, dl_dphi, dl_dtheta, dl_dsigma):
         """Device torch tensors: dl_dphi (float32, N), dl_dtheta (float64,

@@ -693,6 +693,12 @@ int nblk(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 struct AdjointState {
   int nsteps = 0, every = 0;
+  // two-level checkpointing: outer checkpoints every `outer` steps (0: one
+  // level); the inner checkpoints (every `every` steps) then cover one outer
+  // segment at a time and are rebuilt by a recompute in the backward pass
+  int outer = 0;
+  std::vector<float*> ck1_f, ck1_phi;
+  MassScalars* ck1_mass = nullptr;
   int64_t N = 0;
   int W = 0;
   // checkpoints: f* (27N floats) and phi (N) at steps 0, every, 2 every, ...
@@ -717,10 +723,10 @@ struct AdjointState {
 namespace cacl {
 void adjoint_free(AdjointState* s) {
   if (!s) return;
-  for (auto* v : {&s->ck_f, &s->ck_phi, &s->t_fprev, &s->t_phipre, &s->t_phig,
-                  &s->t_u, &s->t_a, &s->t_phis})
+  for (auto* v : {&s->ck_f, &s->ck_phi, &s->ck1_f, &s->ck1_phi, &s->t_fprev,
+                  &s->t_phipre, &s->t_phig, &s->t_u, &s->t_a, &s->t_phis})
     for (float* p : *v) cudaFree(p);
-  void* bufs[] = {s->ck_mass, s->t_mass, s->fb, s->fb2, s->phib, s->phisb, s->phigb, s->ub,
+  void* bufs[] = {s->ck_mass, s->ck1_mass, s->t_mass, s->fb, s->fb2, s->phib, s->phisb, s->phigb, s->ub,
                   s->ab, s->face, s->nodeb, s->wd, s->thetab, s->sigmab,
                   s->partial, s->scal, s->row_start, s->row_entry};
   for (void* b : bufs)
@@ -784,6 +790,19 @@ cacl_status build_transpose(cacl_ctx* c, AdjointState* s) {
   return CACL_OK;
 }
 
+// Copy the current state (populations, phi, mass record incl. the rounding
+// key) into a checkpoint.
+cacl_status store_checkpoint(cacl_ctx* c, float* f, float* phi, MassScalars* m) {
+  const int64_t N = c->g.N;
+  ACK(cudaMemcpyAsync(f, c->f[c->fcur], sizeof(float) * Q * N,
+                      cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
+  ACK(cudaMemcpyAsync(phi, c->phi[c->pcur], sizeof(float) * N,
+                      cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
+  ACK(cudaMemcpyAsync(m, c->mass, sizeof(MassScalars), cudaMemcpyDeviceToDevice,
+                      c->stream), "checkpoint");
+  return CACL_OK;
+}
+
 // Step t of a segment's recompute, recording tape slot t. The populations
 // need no copy: the step reads f*^{n-1} from slot t (the checkpoint was
 // restored into slot 0) and the collide-stream writes f*^n straight into
@@ -820,22 +839,43 @@ cacl_status taped_step(cacl_ctx* c, AdjointState* s, int t, int len) {
 extern "C" {
 
 cacl_status cacl_adjoint_forward(cacl_ctx* c, int nsteps, int every) {
-  if (!c || nsteps < 1 || every < 1) return CACL_ERR_ARG;
+  return cacl_adjoint_forward_levels(c, nsteps, every, 0);
+}
+
+cacl_status cacl_adjoint_forward_levels(cacl_ctx* c, int nsteps, int every,
+                                        int outer) {
+  if (!c || nsteps < 1 || every < 1 || outer < 0) return CACL_ERR_ARG;
+  if (outer > 0 && outer % every != 0)
+    return afail(c, CACL_ERR_ARG, "outer_every must be a multiple of ckpt_every");
   if (!c->has_fields) return afail(c, CACL_ERR_STATE, "set_fields first");
   if (c->p.storage != CACL_F32)
     return afail(c, CACL_ERR_ARG, "the adjoint needs FP32 population storage");
   if (c->fcur != c->pcur) return afail(c, CACL_ERR_STATE, "step parts out of phase");
   const int64_t N = c->g.N;
   AdjointState* s = c->adj;
-  if (!s || s->nsteps != nsteps || s->every != every || s->N != N ||
-      s->W != c->wall_count) {
+  if (!s || s->nsteps != nsteps || s->every != every || s->outer != outer ||
+      s->N != N || s->W != c->wall_count) {
     adjoint_free(s);
     c->adj = s = new AdjointState();
     s->nsteps = nsteps;
     s->every = every;
+    s->outer = outer;
     s->N = N;
     s->W = c->wall_count;
-    const int nck = (nsteps + every - 1) / every;
+    // inner checkpoints: the whole rollout (one level) or one outer segment
+    const int span = outer > 0 ? std::min(outer, nsteps) : nsteps;
+    const int nck = (span + every - 1) / every;
+    if (outer > 0) {
+      const int nck1 = (nsteps + outer - 1) / outer;
+      for (int i = 0; i < nck1; ++i) {
+        float *pf, *pp;
+        ACK(alloc(&pf, (size_t)Q * N), "alloc checkpoint");
+        s->ck1_f.push_back(pf);
+        ACK(alloc(&pp, (size_t)N), "alloc checkpoint");
+        s->ck1_phi.push_back(pp);
+      }
+      ACK(alloc(&s->ck1_mass, nck1), "alloc checkpoint");
+    }
     for (int i = 0; i < nck; ++i) {
       float *pf, *pp;
       ACK(alloc(&pf, (size_t)Q * N), "alloc checkpoint");
@@ -876,16 +916,16 @@ cacl_status cacl_adjoint_forward(cacl_ctx* c, int nsteps, int every) {
     const cacl_status st = build_transpose(c, s);
     if (st != CACL_OK) return st;
   }
-  // forward, keeping a checkpoint at the start of every segment
+  // forward, keeping a checkpoint at the start of every segment (outer
+  // segments with two levels)
+  const int stride = outer > 0 ? outer : every;
   for (int n = 0; n < nsteps; ++n) {
-    if (n % every == 0) {
-      const int ck = n / every;
-      ACK(cudaMemcpyAsync(s->ck_f[ck], c->f[c->fcur], sizeof(float) * Q * N,
-                          cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
-      ACK(cudaMemcpyAsync(s->ck_phi[ck], c->phi[c->pcur], sizeof(float) * N,
-                          cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
-      ACK(cudaMemcpyAsync(s->ck_mass + ck, c->mass, sizeof(MassScalars),
-                          cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
+    if (n % stride == 0) {
+      const cacl_status st = store_checkpoint(
+          c, outer > 0 ? s->ck1_f[n / stride] : s->ck_f[n / stride],
+          outer > 0 ? s->ck1_phi[n / stride] : s->ck_phi[n / stride],
+          (outer > 0 ? s->ck1_mass : s->ck_mass) + n / stride);
+      if (st != CACL_OK) return st;
     }
     const cacl_status st = cacl_step(c, 1);
     if (st != CACL_OK) return st;
@@ -927,74 +967,101 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
   ACK(cudaMemsetAsync(s->thetab, 0, sizeof(double) * (W > 0 ? W : 1), st), "seed");
   ACK(cudaMemsetAsync(s->sigmab, 0, sizeof(double), st), "seed");
 
-  const int nseg = (s->nsteps + s->every - 1) / s->every;
   const bool small = (int64_t)Q * N < (int64_t)INT32_MAX;  // 32-bit offsets
   const bool small15 = (int64_t)15 * N < (int64_t)INT32_MAX;  // face buffer
   bool first = true;  // no later step: dL/df* of the final populations is 0
-  for (int seg = nseg - 1; seg >= 0; --seg) {
-    const int n0 = seg * s->every;
-    const int len = std::min(s->every, s->nsteps - n0);
-    // recompute the segment with its tape
-    ACK(cudaMemcpyAsync(s->t_fprev[0], s->ck_f[seg], sizeof(float) * Q * N,
-                        cudaMemcpyDeviceToDevice, st), "restore");
-    ACK(cudaMemcpyAsync(c->phi[c->pcur], s->ck_phi[seg], sizeof(float) * N,
-                        cudaMemcpyDeviceToDevice, st), "restore");
-    ACK(cudaMemcpyAsync(c->mass, s->ck_mass + seg, sizeof(MassScalars),
-                        cudaMemcpyDeviceToDevice, st), "restore");
-    for (int t = 0; t < len; ++t) {
-      const cacl_status r = taped_step(c, s, t, len);
-      if (r != CACL_OK) return r;
+  // outer segments, last first (one segment spanning the rollout with one
+  // level); with two levels each is recomputed once from its outer
+  // checkpoint to rebuild its inner checkpoints
+  const int span = s->outer > 0 ? s->outer : s->nsteps;
+  const int nouter = (s->nsteps + span - 1) / span;
+  for (int J = nouter - 1; J >= 0; --J) {
+    const int m0 = J * span;                          // first step of the segment
+    const int mlen = std::min(span, s->nsteps - m0);  // its steps
+    if (s->outer > 0) {
+      ACK(cudaMemcpyAsync(c->f[c->fcur], s->ck1_f[J], sizeof(float) * Q * N,
+                          cudaMemcpyDeviceToDevice, st), "restore");
+      ACK(cudaMemcpyAsync(c->phi[c->pcur], s->ck1_phi[J], sizeof(float) * N,
+                          cudaMemcpyDeviceToDevice, st), "restore");
+      ACK(cudaMemcpyAsync(c->mass, s->ck1_mass + J, sizeof(MassScalars),
+                          cudaMemcpyDeviceToDevice, st), "restore");
+      for (int n = 0; n < mlen; ++n) {
+        if (n % s->every == 0) {
+          const int ck = n / s->every;
+          const cacl_status r =
+              store_checkpoint(c, s->ck_f[ck], s->ck_phi[ck], s->ck_mass + ck);
+          if (r != CACL_OK) return r;
+        }
+        const cacl_status r = cacl_step(c, 1);
+        if (r != CACL_OK) return r;
+      }
     }
-    for (int t = len - 1; t >= 0; --t) {
-      // A1 correction
-      const int nb_sum = std::min(nblk(N, AT), 1024);
-      adj_correct_sum<<<nb_sum, AT, 0, st>>>(s->phib, s->t_phis[t], c->flags, N, eps,
-                                             s->partial);
-      adj_correct_scalars<<<1, 32, 0, st>>>(s->partial, nb_sum, s->t_mass + t, s->scal);
-      adj_correct_apply<<<nblk(N, AT), AT, 0, st>>>(s->phib, s->t_phis[t], c->flags,
-                                                    N, eps, s->scal, s->phisb);
-      // A2 phi update
-      const dim3 rows((g.nx + 127) / 128, g.ny, g.nz);
-      if (small15) {
-        adj_phase_faces<int><<<rows, 128, 0, st>>>(s->t_phig[t], s->t_u[t], c->flags,
-                                                   s->phisb, s->face, g);
-        adj_phase_gather<int><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face,
-                                                    s->phigb, s->ub, s->ab, g, c->k);
-      } else {
-        adj_phase_faces<int64_t><<<rows, 128, 0, st>>>(s->t_phig[t], s->t_u[t],
-                                                       c->flags, s->phisb, s->face, g);
-        adj_phase_gather<int64_t><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face,
-                                                        s->phigb, s->ub, s->ab, g,
-                                                        c->k);
+    const int nseg = (mlen + s->every - 1) / s->every;
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+      const int n0 = seg * s->every;
+      const int len = std::min(s->every, mlen - n0);
+      // recompute the segment with its tape
+      ACK(cudaMemcpyAsync(s->t_fprev[0], s->ck_f[seg], sizeof(float) * Q * N,
+                          cudaMemcpyDeviceToDevice, st), "restore");
+      ACK(cudaMemcpyAsync(c->phi[c->pcur], s->ck_phi[seg], sizeof(float) * N,
+                          cudaMemcpyDeviceToDevice, st), "restore");
+      ACK(cudaMemcpyAsync(c->mass, s->ck_mass + seg, sizeof(MassScalars),
+                          cudaMemcpyDeviceToDevice, st), "restore");
+      for (int t = 0; t < len; ++t) {
+        const cacl_status r = taped_step(c, s, t, len);
+        if (r != CACL_OK) return r;
       }
-      // A3 collide-stream
-      const int nbl = (int)(rows.x * rows.y * rows.z);
-      // the later step's pulled-population adjoints (none after the last)
-      const float* later = first ? nullptr : s->fb;
-      if (small) {
-        adj_lb_node<int><<<rows, 128, 0, st>>>(s->t_fprev[t], s->t_phig[t], c->flags,
-                                               later, s->ub, s->ab, s->fb2, s->nodeb,
-                                               s->partial, g, c->k, db4, dkp);
-      } else {
-        adj_lb_node<int64_t><<<rows, 128, 0, st>>>(
-            s->t_fprev[t], s->t_phig[t], c->flags, later, s->ub, s->ab, s->fb2,
-            s->nodeb, s->partial, g, c->k, db4, dkp);
+      for (int t = len - 1; t >= 0; --t) {
+        // A1 correction
+        const int nb_sum = std::min(nblk(N, AT), 1024);
+        adj_correct_sum<<<nb_sum, AT, 0, st>>>(s->phib, s->t_phis[t], c->flags, N, eps,
+                                               s->partial);
+        adj_correct_scalars<<<1, 32, 0, st>>>(s->partial, nb_sum, s->t_mass + t, s->scal);
+        adj_correct_apply<<<nblk(N, AT), AT, 0, st>>>(s->phib, s->t_phis[t], c->flags,
+                                                      N, eps, s->scal, s->phisb);
+        // A2 phi update
+        const dim3 rows((g.nx + 127) / 128, g.ny, g.nz);
+        if (small15) {
+          adj_phase_faces<int><<<rows, 128, 0, st>>>(s->t_phig[t], s->t_u[t], c->flags,
+                                                     s->phisb, s->face, g);
+          adj_phase_gather<int><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face,
+                                                      s->phigb, s->ub, s->ab, g, c->k);
+        } else {
+          adj_phase_faces<int64_t><<<rows, 128, 0, st>>>(s->t_phig[t], s->t_u[t],
+                                                         c->flags, s->phisb, s->face, g);
+          adj_phase_gather<int64_t><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face,
+                                                          s->phigb, s->ub, s->ab, g,
+                                                          c->k);
+        }
+        // A3 collide-stream
+        const int nbl = (int)(rows.x * rows.y * rows.z);
+        // the later step's pulled-population adjoints (none after the last)
+        const float* later = first ? nullptr : s->fb;
+        if (small) {
+          adj_lb_node<int><<<rows, 128, 0, st>>>(s->t_fprev[t], s->t_phig[t], c->flags,
+                                                 later, s->ub, s->ab, s->fb2, s->nodeb,
+                                                 s->partial, g, c->k, db4, dkp);
+        } else {
+          adj_lb_node<int64_t><<<rows, 128, 0, st>>>(
+              s->t_fprev[t], s->t_phig[t], c->flags, later, s->ub, s->ab, s->fb2,
+              s->nodeb, s->partial, g, c->k, db4, dkp);
+        }
+        std::swap(s->fb, s->fb2);  // fb: this step's pulled-population adjoints
+        first = false;
+        sum_partials<<<1, 128, 0, st>>>(s->partial, nbl, s->sigmab);
+        if (small)
+          adj_lb_gather<int><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
+        else
+          adj_lb_gather<int64_t><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
+        // A4 ghost map
+        if (W > 0)
+          adj_ghost_node<<<nblk(W, 128), 128, 0, st>>>(
+              s->t_phipre[t], c->w_idx, c->w_donor, c->w_q, c->w_nw, c->w_cot,
+              c->w_theta, s->phigb, s->wd, s->thetab, W, g);
+        adj_ghost_gather<<<nblk(N, AT), AT, 0, st>>>(c->flags, s->phigb, s->row_start,
+                                                     s->row_entry, s->wd, s->phib, N);
+        ACK(cudaGetLastError(), "adjoint step");
       }
-      std::swap(s->fb, s->fb2);  // fb: this step's pulled-population adjoints
-      first = false;
-      sum_partials<<<1, 128, 0, st>>>(s->partial, nbl, s->sigmab);
-      if (small)
-        adj_lb_gather<int><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
-      else
-        adj_lb_gather<int64_t><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
-      // A4 ghost map
-      if (W > 0)
-        adj_ghost_node<<<nblk(W, 128), 128, 0, st>>>(
-            s->t_phipre[t], c->w_idx, c->w_donor, c->w_q, c->w_nw, c->w_cot,
-            c->w_theta, s->phigb, s->wd, s->thetab, W, g);
-      adj_ghost_gather<<<nblk(N, AT), AT, 0, st>>>(c->flags, s->phigb, s->row_start,
-                                                   s->row_entry, s->wd, s->phib, N);
-      ACK(cudaGetLastError(), "adjoint step");
     }
   }
   if (dL_dtheta && W > 0)

@@ -122,6 +122,40 @@ def test_autograd_function_matches_direct_call(gpu_grad):
     assert abs(sg.grad.item() - gpu_grad["dsigma"]) <= 1e-6 * abs(gpu_grad["dsigma"])
 
 
+def test_two_level_checkpoints_match_one_level():
+    """Outer checkpoints every 6 steps (the last outer segment ragged, 20 =
+    6 + 6 + 6 + 2), inner every 2: the backward rebuilds the inner
+    checkpoints by recomputing each outer segment, and every step is
+    deterministic, so the final field and both gradients equal the
+    one-level ones bit for bit."""
+    import torch
+
+    from paper_2607_25444_b300 import cacl
+    p, solid, phi, theta, patch, r = _case()
+    g = torch.from_numpy(r.reshape(-1).astype(np.float32)).cuda()
+    out = []
+    for outer in (0, 6):
+        s = cacl.Solver(p)
+        s.set_geometry(solid)
+        wl = s.wall_list()
+        s.set_fields(phi)
+        s.set_wall_angles(theta.reshape(-1)[wl["idx"]])
+        s.adjoint_forward(STEPS, 2, outer)
+        dth = torch.zeros(wl["idx"].size, dtype=torch.float64, device="cuda")
+        dsg = torch.zeros(1, dtype=torch.float64, device="cuda")
+        s.adjoint_backward(g, dth, dsg)
+        torch.cuda.synchronize()
+        out.append((s.fields()[0], dth.cpu().numpy(), float(dsg.item())))
+        if outer:
+            with pytest.raises(cacl.CaclError):
+                s.adjoint_forward(STEPS, 4, 6)  # 6 is not a multiple of 4
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+    assert np.abs(out[0][1]).max() > 0.0
+
+
 def test_wettability_inference_reduces_loss():
     """Recover patchwise contact angles from a target footprint: a few
     gradient steps through the adjoint from a uniform 90 deg start lower the
