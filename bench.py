@@ -326,7 +326,7 @@ def run_adjoint(args, torch, cacl, stream):
     ev[1].record(stream)
     s.set_fields(phi)
     ev[2].record(stream)
-    s.adjoint_forward(steps, every)
+    s.adjoint_forward(steps, every, args.adjoint_outer)
     ev[3].record(stream)
     g = torch.zeros(n * n * n, dtype=torch.float32, device="cuda")
     g.view(n, n, n)[1] = 1.0  # dL/dphi of the footprint layer sum
@@ -341,7 +341,7 @@ def run_adjoint(args, torch, cacl, stream):
     t_bwd = ev[4].elapsed_time(ev[5])
     s.close()
     return {"workload": "96^3 flat walls, theta in 8x8 patches U[45,135] deg, R=16",
-            "steps": steps, "ckpt_every": every,
+            "steps": steps, "ckpt_every": every, "outer_every": args.adjoint_outer,
             "forward_ms_per_step": t_plain / steps,
             "checkpointed_forward_ms_per_step": t_fwd / steps,
             "backward_ms_per_step": t_bwd / steps,
@@ -574,6 +574,9 @@ def main():
                     help="rollout length of the adjoint/forward cost measurement")
     ap.add_argument("--adjoint-every", type=int, default=50,
                     help="checkpoint interval of that measurement")
+    ap.add_argument("--adjoint-outer", type=int, default=0,
+                    help="outer checkpoint interval (two-level checkpointing; "
+                         "0 = one level)")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint/forward cost measurement and "
                          "print its JSON (for profiling the adjoint kernels)")
