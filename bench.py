@@ -302,19 +302,20 @@ def run_batched(args, torch, cacl, stream):
 
 def run_adjoint(args, torch, cacl, stream):
     """Adjoint/forward cost on a wettability-inference case shaped like the
-    workload of the adjoint: 96^3, flat walls, theta in 8 x 8 patches drawn
-    from [45, 135] deg (seeded), droplet R = 16, sigma = 0.01, nu = 0.1."""
+    workload of the adjoint: n^3 (96 by default), flat walls, theta in 8 x 8
+    patches drawn from [45, 135] deg (seeded), droplet R = n / 6, sigma =
+    0.01, nu = 0.1."""
     from paper_2607_25444_b300 import inputs as I
-    n = 96
+    n = args.adjoint_grid
     p = I.base_params(n, n, n, sigma=0.01, nu_l=0.1, nu_g=0.1, theta_deg=90.0)
     solid = I.walls_z(n, n, n)
-    phi = I.droplet(n, n, n, (n / 2, n / 2, 0.5), 16.0, p["width"])
+    phi = I.droplet(n, n, n, (n / 2, n / 2, 0.5), n / 6.0, p["width"])
     s = cacl.Solver(p)
     s.set_geometry(solid)
     idx = s.wall_list()["idx"]
     x, y = idx % n, (idx // n) % n
     patches = I.SplitMix64(7).array(64, 45.0, 135.0)
-    theta_w = patches[(y // 12) * 8 + (x // 12)].astype(np.float32)
+    theta_w = patches[(y * 8 // n) * 8 + (x * 8 // n)].astype(np.float32)
     steps, every = args.adjoint_steps, args.adjoint_every
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     s.set_fields(phi)
@@ -328,6 +329,8 @@ def run_adjoint(args, torch, cacl, stream):
     ev[2].record(stream)
     s.adjoint_forward(steps, every, args.adjoint_outer)
     ev[3].record(stream)
+    torch.cuda.synchronize()
+    free_b, total_b = torch.cuda.mem_get_info()
     g = torch.zeros(n * n * n, dtype=torch.float32, device="cuda")
     g.view(n, n, n)[1] = 1.0  # dL/dphi of the footprint layer sum
     dth = torch.zeros(idx.size, dtype=torch.float64, device="cuda")
@@ -340,7 +343,11 @@ def run_adjoint(args, torch, cacl, stream):
     t_fwd = ev[2].elapsed_time(ev[3])
     t_bwd = ev[4].elapsed_time(ev[5])
     s.close()
-    return {"workload": "96^3 flat walls, theta in 8x8 patches U[45,135] deg, R=16",
+    return {"workload": f"{n}^3 flat walls, theta in 8x8 patches U[45,135] deg, "
+                        f"R={n / 6.0:g}",
+            "device_gb_in_use_after_forward": (total_b - free_b) / 1e9,
+            "dl_dsigma": float(dsg.item()),
+            "dl_dtheta_abs_max": float(dth.abs().max().item()),
             "steps": steps, "ckpt_every": every, "outer_every": args.adjoint_outer,
             "forward_ms_per_step": t_plain / steps,
             "checkpointed_forward_ms_per_step": t_fwd / steps,
@@ -574,6 +581,8 @@ def main():
                     help="rollout length of the adjoint/forward cost measurement")
     ap.add_argument("--adjoint-every", type=int, default=50,
                     help="checkpoint interval of that measurement")
+    ap.add_argument("--adjoint-grid", type=int, default=96,
+                    help="cube edge of the adjoint cost measurement")
     ap.add_argument("--adjoint-outer", type=int, default=0,
                     help="outer checkpoint interval (two-level checkpointing; "
                          "0 = one level)")

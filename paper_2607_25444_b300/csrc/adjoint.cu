@@ -455,7 +455,17 @@ __device__ __forceinline__ void collide_adj(const float (&f)[Q], float phi0,
   inv_rhob += mu * nub;
   float rhob = rbb - inv_rho * inv_rho * inv_rhob;
   phi0b += k.dmu * mub + k.drho * rhob;
-  // compressive vector a_c = phi (1 - phi) g / |g|
+  // compressive vector a_c = phi (1 - phi) g / |g|. The rotation of the
+  // unit normal h = g / |g| has derivative phi (1 - phi) (I - h h) / |g|,
+  // whose gain phi (1 - phi) / |g| is width / 4 on an equilibrium interface
+  // but unbounded on the plateaus of the bulk phases (|g| << |phi (1 - phi)|,
+  // e.g. where phi overshoots 1 inside a drop): there the exact
+  // linearisation of the discrete map grows without bound over long
+  // rollouts although the map's response stays below |phi (1 - phi)|. The
+  // rotation term is therefore kept only inside the interface band of the
+  // volume correction, eps_phi < phi < 1 - eps_phi (Eq.
+  // interface_weight_mass_correction), and the normal is held fixed in the
+  // bulk phases.
   const float g2 = gx * gx + gy * gy + gz * gz;
   if (g2 >= 1e-24f) {
     const float ig = rsqrtf(g2);
@@ -463,9 +473,11 @@ __device__ __forceinline__ void collide_adj(const float (&f)[Q], float phi0,
     const float hb = hx * acbx + hy * acby + hz * acbz;
     const float pp = phi0 * (1.f - phi0);
     phi0b += (1.f - 2.f * phi0) * hb;
-    gbx += pp * ig * (acbx - hb * hx);
-    gby += pp * ig * (acby - hb * hy);
-    gbz += pp * ig * (acbz - hb * hz);
+    if (phi0 > k.eps_phi && phi0 < 1.f - k.eps_phi) {
+      gbx += pp * ig * (acbx - hb * hx);
+      gby += pp * ig * (acby - hb * hy);
+      gbz += pp * ig * (acbz - hb * hz);
+    }
   }
   // moments
 #pragma unroll
