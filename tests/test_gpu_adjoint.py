@@ -156,6 +156,57 @@ def test_two_level_checkpoints_match_one_level():
     assert np.abs(out[0][1]).max() > 0.0
 
 
+def test_long_rollout_256_matches_finite_difference():
+    """Long horizon at the benchmark's size: 256^3, contact angles in 8 x 8
+    patches from [45, 135] deg, a drop of radius 42.7, 1000 steps with
+    two-level checkpoints (every 10 inside outer segments of 100, about
+    75 GB). dL/dsigma of the first-layer sum from the adjoint agrees with a
+    central difference of the GPU forward (h = 1e-5). The tolerance is 3e-3:
+    the FP32 difference itself moves by 7e-4 between h = 1e-5 and 1e-6. This
+    case exposed the unbounded linearisation of the compressive term's unit
+    normal on bulk plateaus (the gradient reached 5e8 after 1000 steps before
+    the normal was frozen outside the interface band)."""
+    import torch
+
+    from paper_2607_25444_b300 import cacl
+    n, steps = 256, 1000
+    p = I.base_params(n, n, n, sigma=0.01, nu_l=0.1, nu_g=0.1, theta_deg=90.0)
+    solid = I.walls_z(n, n, n)
+    phi = I.droplet(n, n, n, (n / 2, n / 2, 0.5), n / 6.0, p["width"])
+    s = cacl.Solver(p)
+    s.set_geometry(solid)
+    idx = s.wall_list()["idx"]
+    x, y = idx % n, (idx // n) % n
+    patches = I.SplitMix64(7).array(64, 45.0, 135.0)
+    theta_w = patches[(y * 8 // n) * 8 + (x * 8 // n)].astype(np.float32)
+
+    def loss(sig):
+        s.set_sigma(sig)
+        s.set_fields(phi)
+        s.set_wall_angles(theta_w)
+        s.step(steps)
+        return float(s.fields()[0][1].astype(np.float64).sum())
+
+    h = 1e-5
+    fd = (loss(0.01 + h) - loss(0.01 - h)) / (2 * h)
+    s.set_sigma(0.01)
+    s.set_fields(phi)
+    s.set_wall_angles(theta_w)
+    s.adjoint_forward(steps, 10, 100)
+    g = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
+    g.view(n, n, n)[1] = 1.0
+    dth = torch.zeros(idx.size, dtype=torch.float64, device="cuda")
+    dsg = torch.zeros(1, dtype=torch.float64, device="cuda")
+    s.adjoint_backward(g, dth, dsg)
+    torch.cuda.synchronize()
+    ad = float(dsg.item())
+    s.close()
+    print(f"256^3 x {steps}: dsigma adjoint {ad:.6e} fd {fd:.6e} "
+          f"rel {abs(ad - fd) / abs(fd):.2e}")
+    assert np.isfinite(dth.cpu().numpy()).all()
+    assert abs(ad - fd) <= 3e-3 * abs(fd), (ad, fd)
+
+
 def test_wettability_inference_reduces_loss():
     """Recover patchwise contact angles from a target footprint: a few
     gradient steps through the adjoint from a uniform 90 deg start lower the
