@@ -92,6 +92,25 @@ def sphere_solid(nx, ny, nz, centre, radius):
     return (r2 <= radius * radius).astype(np.uint8)
 
 
+def cylinder_solid(nx, ny, nz, centre_xy, radius):
+    """Solid cylinder along z (curved-wall geometry checks), periodic box."""
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx),
+                          indexing="ij")
+    r2 = (x - centre_xy[0]) ** 2 + (y - centre_xy[1]) ** 2
+    return (r2 <= radius * radius).astype(np.uint8)
+
+
+def rough_wall_z(nx, ny, nz, amplitude, seed=SEED):
+    """Walls at z = 0 and nz - 1, the bottom one rough: column (x, y) is
+    solid up to a seeded height drawn uniformly from 0 .. amplitude."""
+    h = np.floor(fast_uniform((ny, nx), seed=seed, lo=0.0,
+                              hi=amplitude + 1.0)).astype(np.int64)
+    z = np.arange(nz)[:, None, None]
+    solid = (z <= h[None]).astype(np.uint8)
+    solid[-1] = 1
+    return solid
+
+
 # ------------------------------------------------------------ phase fields
 
 def droplet(nx, ny, nz, centre, radius, width, dtype=np.float32):

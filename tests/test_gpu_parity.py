@@ -49,6 +49,8 @@ def _geometries():
     rnd = (I.fast_uniform((n, n, n), seed=21) < 0.4).astype(np.uint8)
     yield "random", rnd, (1, 1, 1)
     yield "sphere", I.sphere_solid(21, 21, 21, (10, 10, 10), 6.0), (1, 1, 1)
+    yield "cylinder", I.cylinder_solid(29, 29, 6, (14.0, 14.0), 9.5), (1, 1, 1)
+    yield "rough", I.rough_wall_z(24, 20, 14, 3, seed=5), (1, 1, 0)
     lone = np.ones((5, 5, 5), np.uint8)
     lone[2, 2, 2] = 0
     yield "lone", lone, (1, 1, 1)
@@ -161,6 +163,39 @@ def test_ragged_sizes_and_patterned_angles():
     ophi, ou, op = o.fields()
     assert _rel(gphi, ophi) < 3 * TOL_1STEP
     assert _rel(gu, ou) < 3 * TOL_1STEP
+
+
+@pytest.mark.parametrize("kind", ["cylinder", "rough", "sphere"])
+def test_curved_and_rough_walls_steps(kind):
+    """A drop in contact with a cylinder (periodic box), a rough floor
+    (seeded column heights 0..3) or a ball, with patterned contact angles:
+    ghosts on staircase walls with quantised normals, bounce-back on
+    irregular links; three full steps against the oracle."""
+    if kind == "cylinder":
+        nx, ny, nz = 32, 30, 12
+        solid = I.cylinder_solid(nx, ny, nz, (15.5, 14.5), 7.0)
+        phi = I.droplet(nx, ny, nz, (24.0, 14.5, 6.0), 6.0, 4.0)
+        periodic = (1, 1, 1)
+    elif kind == "rough":
+        nx, ny, nz = 30, 26, 16
+        solid = I.rough_wall_z(nx, ny, nz, 3, seed=9)
+        phi = I.droplet(nx, ny, nz, (15.0, 13.0, 3.0), 7.0, 4.0)
+        periodic = (1, 1, 0)
+    else:
+        nx, ny, nz = 28, 28, 28
+        solid = I.sphere_solid(nx, ny, nz, (13.5, 13.5, 10.0), 6.5)
+        phi = I.droplet(nx, ny, nz, (13.5, 13.5, 19.0), 6.0, 4.0)
+        periodic = (1, 1, 1)
+    p = I.base_params(nx, ny, nz, sigma=0.01, rho_g=0.2, periodic=periodic)
+    theta = (40.0 + 100.0 * I.fast_uniform((nz, ny, nx), seed=13)).astype(np.float32)
+    g, o = _pair(p, solid, phi, theta=theta)
+    g.step(3)
+    o.step(3)
+    gphi, gu, gp = g.fields()
+    ophi, ou, op = o.fields()
+    assert _rel(gphi, ophi) < 3 * TOL_1STEP
+    assert _rel(gu, ou) < 3 * TOL_1STEP
+    assert _rel(gp, op) < 3 * TOL_1STEP
 
 
 def test_no_walls_fully_periodic():
