@@ -391,6 +391,54 @@ def run_theta_recovery(args):
                       "results": out}), flush=True)
 
 
+def run_curved_wall(args):
+    """Contact angle on a curved wall next to a flat one, on 2D slabs (the
+    D3Q27 lattice one node thick): a drop of radius 30 relaxes for
+    args.cw_steps steps (a) on a flat wall (256 x 128, walls at y = 0 and
+    127) and (b) on a solid disc of radius 40 (256 x 256, periodic); sigma =
+    0.01, W = 4, equal densities and viscosities. The angle comes from the
+    circle fitted to the phi = 1/2 crossings farther than 3.5 from the wall
+    surface (taken halfway between the solid and the fluid nodes)."""
+    import torch
+
+    from paper_2607_25444_b300 import cacl
+    from paper_2607_25444_b300 import diagnostics as Dg
+    from paper_2607_25444_b300 import inputs as I
+    torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    steps = args.cw_steps
+    out = []
+    for th in args.angles:
+        nx, ny = 256, 128
+        p = I.base_params(nx, ny, 1, dim=2, periodic=(1, 0, 1), sigma=0.01,
+                          theta_deg=th)
+        s = cacl.Solver(p)
+        s.set_geometry(I.walls_y(nx, ny, 1))
+        s.set_fields(I.droplet(nx, ny, 1, (nx / 2, 0.5, 0.0), 30.0, p["width"]))
+        s.step(steps)
+        s.check_finite()
+        f = s.fields()[0][0]
+        flat = Dg.contact_angle(f[:, None, :], z_wall=0.5, y=0, z_min=4.0)
+        s.close()
+        n, rc, cx, cy = 256, 40.0, 128.0, 100.0
+        p = I.base_params(n, n, 1, dim=2, periodic=(1, 1, 1), sigma=0.01,
+                          theta_deg=th)
+        s = cacl.Solver(p)
+        s.set_geometry(I.cylinder_solid(n, n, 1, (cx, cy), rc))
+        s.set_fields(I.droplet(n, n, 1, (cx, cy + rc + 0.5, 0.0), 30.0, p["width"]))
+        s.step(steps)
+        s.check_finite()
+        f = s.fields()[0][0]
+        disc = Dg.contact_angle_on_disc(f, (cx, cy), rc + 0.5, min_gap=3.5)
+        s.close()
+        rec = {"theta": th, "flat": flat, "disc": disc, "steps": steps}
+        out.append(rec)
+        print(json.dumps(rec), flush=True)
+    print(json.dumps({"metric": "contact angle on a flat wall and on a disc "
+                                "of radius 40 (2D slab, drop radius 30)",
+                      "results": out}), flush=True)
+
+
 def run_cuda(args):
     import torch
     rank, world, local = dist_env()
@@ -581,6 +629,11 @@ def main():
                     help="rollout length of the adjoint/forward cost measurement")
     ap.add_argument("--adjoint-every", type=int, default=50,
                     help="checkpoint interval of that measurement")
+    ap.add_argument("--curved-wall", action="store_true",
+                    help="contact angle of a 2D drop on a flat wall and on a "
+                         "disc, for each of --angles")
+    ap.add_argument("--cw-steps", type=int, default=40000,
+                    help="relaxation steps of --curved-wall")
     ap.add_argument("--adjoint-grid", type=int, default=96,
                     help="cube edge of the adjoint cost measurement")
     ap.add_argument("--adjoint-outer", type=int, default=0,
@@ -594,6 +647,9 @@ def main():
         args.warmup = 3
     if args.theta_recovery:
         run_theta_recovery(args)
+        return
+    if args.curved_wall:
+        run_curved_wall(args)
         return
     if args.adjoint_only:
         import torch

@@ -29,6 +29,31 @@ def _crossings(slice2d, level=0.5):
     return np.concatenate(xs), np.concatenate(zs)
 
 
+def fit_circle(x, z):
+    """Algebraic least-squares circle through the points (Eq.
+    circle_fit_error): returns (x0, z0, R)."""
+    x = np.asarray(x, np.float64)
+    z = np.asarray(z, np.float64)
+    A = np.stack([2 * x, 2 * z, np.ones_like(x)], axis=1)
+    x0, z0, c = np.linalg.lstsq(A, x * x + z * z, rcond=None)[0]
+    return x0, z0, math.sqrt(c + x0 * x0 + z0 * z0)
+
+
+def contact_angle_on_disc(phi2d, centre, radius, min_gap=3.5):
+    """Angle (degrees, through the liquid) between a drop and a circular
+    wall in a 2D field phi2d[y, x]: the circle fitted to the phi = 1/2
+    crossings farther than radius + min_gap from the wall's centre has
+    centre C and radius r; with d = |C - centre| and R = radius, the angle
+    between the outward normals of the drop and of the wall at their
+    intersection gives cos(theta) = (r^2 + R^2 - d^2) / (2 r R)."""
+    x, y = _crossings(phi2d)
+    keep = np.hypot(x - centre[0], y - centre[1]) > radius + min_gap
+    x0, y0, r = fit_circle(x[keep], y[keep])
+    d2 = (x0 - centre[0]) ** 2 + (y0 - centre[1]) ** 2
+    c = (r * r + radius * radius - d2) / (2.0 * r * radius)
+    return math.degrees(math.acos(min(1.0, max(-1.0, c))))
+
+
 def contact_angle(phi, z_wall=0.5, y=None, z_min=None):
     """Angle (degrees) through the liquid of the circle fitted to the
     phi = 1/2 crossings of the slice y (default ny/2)."""

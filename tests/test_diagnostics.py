@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 
 from paper_2607_25444_b300 import diagnostics as D
 
@@ -35,3 +36,19 @@ def test_extent_of_a_rod():
     x = np.arange(64, dtype=float)
     phi[2, 3] = 0.5 * (np.tanh(2 * (x - 10.25) / 4) - np.tanh(2 * (x - 40.75) / 4))
     assert abs(D.max_extent(phi) - 30.5) < 0.05
+
+
+@pytest.mark.parametrize("theta", [45.0, 90.0, 135.0])
+def test_contact_angle_on_disc_synthetic(theta):
+    """A tanh drop of radius 30 whose circle meets a wall circle of radius
+    40 at a known angle (centres d apart with d^2 = r^2 + R^2 - 2 r R cos
+    theta): the disc diagnostic returns that angle."""
+    r, R = 30.0, 40.0
+    d = math.sqrt(r * r + R * R - 2 * r * R * math.cos(math.radians(theta)))
+    n = 200
+    yy, xx = np.mgrid[0:n, 0:n].astype(np.float64)
+    cw = (100.0, 60.0)
+    cd = (100.0, 60.0 + d)
+    phi = 0.5 * (1.0 - np.tanh((np.hypot(xx - cd[0], yy - cd[1]) - r) / 2.0))
+    got = D.contact_angle_on_disc(phi, cw, R, min_gap=3.5)
+    assert abs(got - theta) < 0.05, got
