@@ -21,9 +21,11 @@ struct cacl_batch {
   int lb_variant = 1;
   int phase_variant = 2;
   CaseDesc* d_cases = nullptr;
-  int* d_starts = nullptr;  // four lists of ncases + 1 starts
-  WorkList wl_lb{}, wl_phase{}, wl_ghost{}, wl_corr{};
-  int grid_lb = 0, grid_phase = 0, grid_ghost = 0, grid_corr = 0;
+  int* d_starts = nullptr;  // five lists of ncases + 1 starts
+  // phi update: cases staged through registers (wl_phase) and cases that
+  // qualify for copy staging (wl_phase_copy), as each would run alone
+  WorkList wl_lb{}, wl_phase{}, wl_phase_copy{}, wl_ghost{}, wl_corr{};
+  int grid_lb = 0, grid_phase = 0, grid_phase_copy = 0, grid_ghost = 0, grid_corr = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool plan_ok = false;
   std::vector<int> geom_version;  // of each case when the plan was built
@@ -66,11 +68,12 @@ cacl_status build_plan(cacl_batch* b) {
   std::vector<CaseDesc> desc(nc);
   b->phase_nb.assign(nc, 0);
   b->geom_version.assign(nc, -1);
-  std::vector<int> starts(4 * (nc + 1), 0);
+  std::vector<int> starts(5 * (nc + 1), 0);
   int* s_lb = starts.data();
   int* s_ph = s_lb + (nc + 1);
   int* s_gh = s_ph + (nc + 1);
   int* s_cr = s_gh + (nc + 1);
+  int* s_pc = s_cr + (nc + 1);
   const int row = lb_batch_row(b->lb_variant);
   int ty = 16, zc = 16;
   phase_tile(b->phase_variant, ty, zc);
@@ -103,7 +106,10 @@ cacl_status build_plan(cacl_batch* b) {
     if (d.phase_nb > c->part_blocks)
       return bfail(b, CACL_ERR_STATE, "partial-sum storage too small");
     s_lb[i + 1] = s_lb[i] + ((c->g.nx + row - 1) / row) * c->g.ny * c->g.nz;
-    s_ph[i + 1] = s_ph[i] + d.phase_nb;
+    const bool copy = c->phase_pipe != 1 &&
+                      phase_copy_ok(c->g, c->phi[0], c->phi[1], c->a, c->u, c->flags);
+    s_ph[i + 1] = s_ph[i] + (copy ? 0 : d.phase_nb);
+    s_pc[i + 1] = s_pc[i] + (copy ? d.phase_nb : 0);
     s_gh[i + 1] = s_gh[i] + (c->wall_count + ghost_batch_block() - 1) /
                                 ghost_batch_block();
     const int64_t per = correct_batch_nodes();
@@ -118,6 +124,7 @@ cacl_status build_plan(cacl_batch* b) {
   b->wl_phase = {b->d_starts + (nc + 1), nc, s_ph[nc]};
   b->wl_ghost = {b->d_starts + 2 * (nc + 1), nc, s_gh[nc]};
   b->wl_corr = {b->d_starts + 3 * (nc + 1), nc, s_cr[nc]};
+  b->wl_phase_copy = {b->d_starts + 4 * (nc + 1), nc, s_pc[nc]};
   // persistent grids: as many blocks as stay resident, at most the work
   const int sms = sm_count();
   auto grid_for = [&](int total, int per_sm) {
@@ -128,6 +135,8 @@ cacl_status build_plan(cacl_batch* b) {
                    ? grid_for(b->wl_lb.total, lb_batch_occupancy(b->storage, b->lb_variant))
                    : b->wl_lb.total;
   b->grid_phase = grid_for(b->wl_phase.total, phase_batch_occupancy(b->phase_variant));
+  b->grid_phase_copy =
+      grid_for(b->wl_phase_copy.total, phase_batch_copy_occupancy(b->phase_variant));
   b->grid_ghost = grid_for(b->wl_ghost.total, 8);
   b->grid_corr = grid_for(b->wl_corr.total, 8);
   b->plan_ok = true;
@@ -142,8 +151,13 @@ cudaError_t enqueue_batch_step(cacl_batch* b, int par) {
   if ((e = launch_lb_batch(b->d_cases, b->wl_lb, b->storage, b->lb_variant,
                            b->grid_lb, par, par, b->stream)) != cudaSuccess)
     return e;
-  if ((e = launch_phase_batch(b->d_cases, b->wl_phase, b->phase_variant,
+  if (b->wl_phase.total > 0 &&
+      (e = launch_phase_batch(b->d_cases, b->wl_phase, b->phase_variant,
                               b->grid_phase, par, b->stream)) != cudaSuccess)
+    return e;
+  if (b->wl_phase_copy.total > 0 &&
+      (e = launch_phase_batch_copy(b->d_cases, b->wl_phase_copy, b->phase_variant,
+                                   b->grid_phase_copy, par, b->stream)) != cudaSuccess)
     return e;
   return launch_correct_batch(b->d_cases, (int)b->cases.size(), b->wl_corr,
                               b->grid_corr, par, b->stream);
@@ -196,7 +210,7 @@ cacl_status cacl_batch_create(const cacl_params* params, int ncases,
     b->cases.push_back(c);
   }
   if (cudaMalloc(&b->d_cases, sizeof(CaseDesc) * ncases) != cudaSuccess ||
-      cudaMalloc(&b->d_starts, sizeof(int) * 4 * (ncases + 1)) != cudaSuccess) {
+      cudaMalloc(&b->d_starts, sizeof(int) * 5 * (ncases + 1)) != cudaSuccess) {
     cacl_batch_destroy(b);
     return CACL_ERR_CUDA;
   }

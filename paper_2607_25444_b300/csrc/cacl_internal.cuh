@@ -400,6 +400,12 @@ int ghost_batch_block();
 cudaError_t launch_phase_batch(const CaseDesc* cases, WorkList wl, int variant,
                                int grid, int pc, cudaStream_t st);
 int phase_batch_occupancy(int variant);
+// the same over cases that qualify for copy staging (phase_copy_ok)
+cudaError_t launch_phase_batch_copy(const CaseDesc* cases, WorkList wl, int variant,
+                                    int grid, int pc, cudaStream_t st);
+int phase_batch_copy_occupancy(int variant);
+bool phase_copy_ok(const Grid& g, const void* phi_in, const void* phi_out,
+                   const void* a, const void* u, const void* flags);
 void phase_tile(int variant, int& ty, int& zc);
 cudaError_t launch_correct_batch(const CaseDesc* cases, int ncases, WorkList wl,
                                  int grid, int pc, cudaStream_t st);

@@ -813,16 +813,67 @@ CopyKernel copy_kernel(int variant) {
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Batched phi update over cases that qualify for copy staging: virtual
+// block b is tile (bx, by, bz) of its case, staged as in phase_update_copy.
+template <int TY, int ZC, int MINB>
+__global__ void __launch_bounds__(TX * TY / 2, MINB)
+phase_update_batch_copy(const CaseDesc* __restrict__ cases, WorkList wl, int pc) {
+  extern __shared__ __align__(16) float dsm[];
+  __shared__ CaseCursor cur;
+  if (threadIdx.x == 0 && threadIdx.y == 0) cur.begin();
+  __syncthreads();
+  int b0, b1;
+  block_range(wl, b0, b1);
+  for (int b = b0; b < b1; ++b) {
+    cur.seek(cases, wl, b);
+    const CaseDesc& cd = cur.d;
+    const int local = b - cur.cstart;
+    const int nbx = (cd.g.nx + TX - 1) / TX, nby = (cd.g.ny + TY - 1) / TY;
+    __syncthreads();  // the previous tile's shared-memory reads are done
+    phase_tile_copy<TY, ZC, COPY_D>(local % nbx, (local / nbx) % nby,
+                                    local / (nbx * nby), local, cd.phi[pc], cd.a,
+                                    cd.phi[1 - pc], cd.u, cd.flags, cd.partials,
+                                    cd.phase_nb, cd.g, cd.k, dsm);
+  }
+}
+
+CopyKernel copy_batch_kernel(int variant) {
+  switch (variant) {
+    case 1: return {(void*)phase_update_batch_copy<8, 16, 4>, CopyTile<8, COPY_D>::bytes};
+    case 2: return {(void*)phase_update_batch_copy<8, 32, 4>, CopyTile<8, COPY_D>::bytes};
+    case 3: return {(void*)phase_update_batch_copy<16, 32, 2>, CopyTile<16, COPY_D>::bytes};
+    default: return {(void*)phase_update_batch_copy<16, 16, 2>, CopyTile<16, COPY_D>::bytes};
+  }
+}
 }  // namespace
 
 cudaError_t phase_init_attributes() {
   for (int v = 0; v < 4; ++v) {
-    const CopyKernel ck = copy_kernel(v);
-    const cudaError_t e = cudaFuncSetAttribute(
-        ck.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ck.smem);
-    if (e != cudaSuccess) return e;
+    for (const CopyKernel ck : {copy_kernel(v), copy_batch_kernel(v)}) {
+      const cudaError_t e = cudaFuncSetAttribute(
+          ck.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ck.smem);
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
+}
+
+int phase_batch_copy_occupancy(int variant) {
+  int nb = 0;
+  const PhaseShape s = phase_shape(variant);
+  const CopyKernel ck = copy_batch_kernel(variant);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ck.fn, TX * s.ty / 2, ck.smem);
+  return nb;
+}
+
+cudaError_t launch_phase_batch_copy(const CaseDesc* cases, WorkList wl, int variant,
+                                    int grid, int pc, cudaStream_t st) {
+  const PhaseShape s = phase_shape(variant);
+  const CopyKernel ck = copy_batch_kernel(variant);
+  void* args[] = {(void*)&cases, (void*)&wl, (void*)&pc};
+  return cudaLaunchKernel(ck.fn, dim3(grid), dim3(TX, s.ty / 2, 1), args, ck.smem,
+                          st);
 }
 
 bool phase_copy_ok(const Grid& g, const void* phi_in, const void* phi_out,
