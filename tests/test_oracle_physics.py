@@ -35,6 +35,55 @@ def test_poiseuille_body_force():
     assert np.abs(ux[1:-1] - exact[1:-1]).max() < 1e-3 * exact.max()
 
 
+def _layered_channel(rho_g, nu_l, nu_g, H=48, g=1e-6, W=4.0, steps=20000):
+    """Two-phase channel flow along x between halfway bounce-back walls at
+    y = 1/2 and y = H + 1/2 (2D, one node in x): liquid (phi = 1) in the
+    lower half, gas above, a flat tanh interface of width W at mid-height, a
+    body force F_ext = (rho(phi) - rho_g) g along x that acts on the liquid
+    only. Returns the oracle's u_x(y), the continuum profile and the node
+    heights."""
+    from scipy.integrate import cumulative_trapezoid
+    ny = H + 2
+    p = I.base_params(1, ny, 1, dim=2, periodic=(1, 0, 1), rho_l=1.0,
+                      rho_g=rho_g, nu_l=nu_l, nu_g=nu_g, gravity=(g, 0, 0),
+                      sigma=0.01, width=W)
+    o = O.Oracle(p)
+    o.set_geometry(I.walls_y(1, ny, 1))
+    y = np.arange(ny, dtype=float)
+    h = 0.5 + H / 2
+    o.set_fields((0.5 * (1 + np.tanh(2 * (h - y) / W))).reshape(1, ny, 1))
+    o.step(steps)
+    ux = o.fields()[1][0, 0, :, 0]
+    # steady shear flow of the continuum with the same diffuse layers:
+    # d/dy (mu du/dy) = -(rho - rho_g) g, u = 0 on both walls, with
+    # mu = rho_g nu_g + (rho_l nu_l - rho_g nu_g) phi and the same tanh phi
+    yy = np.linspace(0.5, ny - 1.5, 200001)
+    ph = 0.5 * (1 + np.tanh(2 * (h - yy) / W))
+    mu = rho_g * nu_g + (nu_l - rho_g * nu_g) * ph
+    F = cumulative_trapezoid((1.0 - rho_g) * ph * g, yy, initial=0.0)
+    inv_mu = cumulative_trapezoid(1.0 / mu, yy, initial=0.0)
+    f_mu = cumulative_trapezoid(F / mu, yy, initial=0.0)
+    exact = (f_mu[-1] / inv_mu[-1]) * inv_mu - f_mu
+    return ux, np.interp(y, yy, exact), y, h
+
+
+@pytest.mark.parametrize("rho_g,nu_l,nu_g", [(0.1, 0.1, 0.1), (0.05, 0.05, 0.1)])
+def test_layered_two_phase_channel_flow(rho_g, nu_l, nu_g):
+    """Pins the viscous correction F_nu (Eqs. Fsplit, Fnu, mu_mix_linear):
+    with a density jump across the layers (ratio 10 or 20) and a dynamic
+    viscosity ratio of 10, the shear stress mu du/dy is continuous across
+    the interface only if F_nu = -(nu omega / c_s^2) Pi . grad rho restores
+    the variable-density viscous term; without it the lattice carries
+    nu du/dy instead. Away from the interface band the oracle's steady
+    profile must match the continuum one within 2.5 % of its maximum
+    (it does to 0.8 %; with F_nu dropped the error is 29-43 %, with its
+    sign flipped 60 %)."""
+    ux, exact, y, h = _layered_channel(rho_g, nu_l, nu_g)
+    far = (np.abs(y - h) > 8.0) & (y >= 1) & (y <= len(y) - 2)
+    err = np.abs(ux - exact)[far].max() / np.abs(exact).max()
+    assert err < 0.025, err
+
+
 def test_shear_wave_decay_rate():
     """u_x = U sin(k y) decays as exp(-nu k^2 t) (Eq. nuomega)."""
     ny = 32
@@ -147,20 +196,22 @@ def test_d3q27_slab_matches_d2q9_on_flat_walls():
 @pytest.mark.slow
 def test_static_contact_angle_2d():
     """2D static droplet (128 x 64, R = 20, W = 4): the measured angle
-    follows the imposed one and lies on the correct side of 90 deg. Sect. 3.1
-    reports deviations of a few degrees at R0 = 40 in 3D; at R = 20 in 2D the
-    oracle measures about 56 deg for 60 and 128 deg for 120."""
+    follows the imposed one within 8 deg and lies on the correct side of
+    90 deg. Sect. 3.1 reports deviations of a few degrees at R0 = 40 in 3D;
+    at R = 20 in 2D the oracle settles (10000 to 40000 steps agree within
+    0.01 deg) at 55.7 deg for 60 and 127.4 deg for 120: the first-order
+    extrapolation of the wetting condition under-shoots a hydrophilic angle
+    and over-shoots a hydrophobic one."""
     got = {}
     for th in (60.0, 120.0):
         p, solid, phi = I.static_droplet_2d(th)
         o = O.Oracle(p)
         o.set_geometry(solid)
         o.set_fields(phi.astype(np.float64))
-        o.step(4000)
+        o.step(10000)
         got[th], _ = Dg.contact_angle(o.fields()[0][0], 0.5)
-    assert abs(got[60.0] - 60.0) < 10.0, got
-    assert abs(got[120.0] - 120.0) < 10.0, got
-    assert got[60.0] < 85.0 < 95.0 < got[120.0]
+    assert 52.0 < got[60.0] < 60.0, got
+    assert 120.0 < got[120.0] < 128.0, got
 
 
 def test_contact_angle_fit_on_exact_circle():
