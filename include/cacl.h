@@ -4,7 +4,7 @@
  * One time step of the conservative Allen-Cahn lattice Boltzmann scheme with
  * the geometric wetting boundary condition of arXiv 2607.25444:
  *   1. ghost phi values at wall nodes from the reconstructed wall normal and
- *      a donor fluid node at the imposed contact angle (Sect. 2.3,
+ *      a donor fluid node at the imposed contact angle (Sect. 2.2,
  *      Eqs. local_wall_normal .. contact_angle_localization, Algorithm 1);
  *   2. the D3Q27 pull collide-stream: third-order Hermite equilibrium,
  *      recursive regularisation, Guo forcing with the chemical-potential
@@ -12,8 +12,8 @@
  *      (Sect. 2.1, Eqs. lbe .. lap_iso);
  *   3. the conservative Allen-Cahn update with MUSCL-minmod advection,
  *      isotropic diffusion and the isotropic compressive divergence
- *      (Sect. 2.2, Eq. phi_update_muscl);
- *   4. the global volume correction over the interface band (Sect. 2.4,
+ *      (Sect. 2.1.1, Eq. phi_update_muscl);
+ *   4. the global volume correction over the interface band (Sect. 2.3,
  *      Eqs. tentative_phase_field_mass .. mass_corrected_phi).
  *
  * Conventions for every call:
@@ -64,7 +64,7 @@ typedef enum {
 } cacl_storage;
 
 /*
- * Problem statement (Sect. 2.1-2.4). All quantities in lattice units.
+ * Problem statement (Sect. 2.1-2.3). All quantities in lattice units.
  *   width      interface thickness delta (Eq. kappa_delta); > 0
  *   mobility   interface diffusivity D; >= 0. kappa = 4 D / delta.
  *   sigma      surface tension; beta = 12 sigma/delta, kappa_phi = 3 sigma
@@ -105,7 +105,7 @@ void cacl_destroy(cacl_ctx* ctx);
 /* Text of the last error recorded on ctx ("" if none). */
 const char* cacl_last_error(const cacl_ctx* ctx);
 
-/* Occupancy (host, N bytes, 1 = solid) -> flags, wall list (Sect. 2.3,
+/* Occupancy (host, N bytes, 1 = solid) -> flags, wall list (Sect. 2.2,
  * Eqs. local_wall_normal .. donor_to_solid). For every solid node with fluid
  * neighbours: integer normal n~6 = sum over fluid links of 6 w_q (-c_q)
  * (w_q = 1, 1/2, 1/3), unit normal n_w = n~6/|n~6| rounded to FP32, donor
@@ -267,10 +267,16 @@ cacl_status cacl_batch_autotune(cacl_batch* batch, int steps, int* lb_variant,
  * (CACL_ERR_ARG when nx is not a multiple of 4 or nz < 2). Both give
  * bit-identical results. CACL_OPT_LB_PIPE selects how the collide-stream
  * reads its 27 pulled population rows and 9 phi rows: 0 = direct loads
- * through the cache (the default), 1 = row runs staged in shared memory by
- * bulk asynchronous copies through a two-stage ring of persistent blocks
- * (CACL_ERR_ARG unless nx is a multiple of 4 and of 16 bytes' worth of
- * populations); bit-identical results. Defaults: tile 2, pipelines 0.
+ * through the cache with two x-adjacent nodes per thread, one aligned
+ * access per pair and packed pair arithmetic (the default; when nx is odd
+ * or 27 N >= 2^31 it runs one node per thread), 1 = row runs staged in
+ * shared memory by bulk asynchronous copies through a two-stage ring of
+ * persistent blocks (CACL_ERR_ARG unless nx is a multiple of 4 and of 16
+ * bytes' worth of populations), 2 = direct loads, one node per thread,
+ * 3 = tiles of 128 nodes copied into shared memory and stored back by the
+ * tensor memory accelerator (when nx is a multiple of 8; else as 0); all
+ * bit-identical at fluid nodes (the tiled form writes f* = 0 at solid
+ * nodes, the others leave them). Defaults: tile 2, pipelines 0.
  * Returns CACL_ERR_ARG for an unknown option or value. */
 typedef enum {
   CACL_OPT_PHASE_TILE = 1,
@@ -296,7 +302,14 @@ cacl_status cacl_get_info(const cacl_ctx* ctx, int64_t* nodes,
  *   phi     device, n floats, corrected in place at fluid nodes:
  *           phi += lambda chi(phi), chi = phi (1 - phi) inside
  *           (eps_phi, 1 - eps_phi), lambda = (m_ref - M*) / W (0 if W = 0),
- *           M* and W the FP64 sums of phi and chi over fluid nodes
+ *           M* and W the FP64 sums of phi and chi over fluid nodes. The sum
+ *           phi + lambda chi is rounded to FP32 without bias, as in the
+ *           context's correction (cacl_volume_correct): the exact residual
+ *           decides, against a hashed uniform number, whether to move one
+ *           unit in the last place, so corrections below the FP32
+ *           resolution of phi still hold the mass on average over repeated
+ *           calls. The hash key is a per-device call counter the library
+ *           keeps in the scratch array (zero when the library is loaded).
  *   solid   device, n bytes, nonzero = solid (left untouched)
  *   n       1 <= n <= 67,108,864 (4096 x 16384); larger n returns
  *           CACL_ERR_TOO_LARGE before any work is enqueued
@@ -304,12 +317,15 @@ cacl_status cacl_get_info(const cacl_ctx* ctx, int64_t* nodes,
  *   out     device, 3 doubles (M*, W, lambda) or NULL
  *   stream  cudaStream_t or NULL; the call enqueues and returns
  *
+ * phi, solid, out and the stream must belong to the current CUDA device
+ * (pointers on another device, or host pointers, return CACL_ERR_ARG).
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture. Every call shares the one scratch array, so
  * calls that overlap on the GPU (other streams, other host threads) race;
- * serialise them on one stream. Returns CACL_ERR_ARG for null pointers or
- * invalid sizes, CACL_ERR_CUDA for a launch or set-up failure.
+ * serialise them on one stream. Returns CACL_ERR_ARG for null pointers,
+ * invalid sizes or pointers not on the current device, CACL_ERR_CUDA for a
+ * launch or set-up failure.
  */
 cacl_status cacl_volume_correct_noalloc(float* phi, const uint8_t* solid,
                                         int64_t n, double m_ref,

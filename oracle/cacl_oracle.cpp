@@ -10,11 +10,11 @@
  *
  * Order of one step n (state f*^{n-1}, phi^n incl. ghosts -> f*^n, u^n,
  * phi^{n+1}):
- *   1. ghost update over the wall list, Jacobi (Sect. 2.3, Algorithm 1)
+ *   1. ghost update over the wall list, Jacobi (Sect. 2.2, Algorithm 1)
  *   2. LB pull collide-stream with forces (Sect. 2.1)
  *   3. CAC update with MUSCL-minmod advection, isotropic diffusion and the
- *      isotropic compressive divergence (Sect. 2.2, Eq. phi_update_muscl)
- *   4. global volume correction (Sect. 2.4, Eqs. mass_defect..mass_corrected_phi)
+ *      isotropic compressive divergence (Sect. 2.1.1, Eq. phi_update_muscl)
+ *   4. global volume correction (Sect. 2.3, Eqs. mass_defect..mass_corrected_phi)
  *
  * Readings of points where the paper is silent (each is listed in the design
  * notes of the repository):
@@ -164,7 +164,7 @@ struct orc_state {
   double M_ref = 0.0, M_star = 0.0, W_sum = 0.0, lambda = 0.0;
   bool has_geom = false, has_fields = false;
   std::string err;
-  // derived constants (Sect. 2.1, Eq. Fcap; Sect. 2.2, Eq. kappa_delta)
+  // derived constants (Sect. 2.1, Eq. Fcap; Sect. 2.1.1, Eq. kappa_delta)
   double beta = 0.0, kappa_phi = 0.0, kappa = 0.0;
 
   long node(int x, int y, int z) const {
@@ -328,7 +328,7 @@ void collide_node(const orc_state* s, const double* fin, double phi,
 }
 
 /* cot(theta_c), theta_c = pi - theta (Eq. internal_contact_angle), with the
- * regularisation of Sect. 2.3 near |sin theta_c| -> 0. */
+ * regularisation of Sect. 2.2 near |sin theta_c| -> 0. */
 double cot_theta_c(double theta_deg) {
   const double thc = kPi - theta_deg * kPi / 180.0;
   const double sn = std::sin(thc), cs = std::cos(thc);
@@ -362,7 +362,7 @@ double chi(double v, double eps) {
   return (v > eps && v < 1.0 - eps) ? v * (1.0 - v) : 0.0;
 }
 
-/* Discrete compressive vector a(y) = phi(1-phi) n at fluid y (Sect. 2.2). */
+/* Discrete compressive vector a(y) = phi(1-phi) n at fluid y (Sect. 2.1.1). */
 void compressive_vector(const orc_state* s, const double* phi, long y,
                         double a[3]) {
   a[0] = a[1] = a[2] = 0.0;
@@ -406,7 +406,7 @@ void orc_destroy(orc_state* s) { delete s; }
 
 const char* orc_error(const orc_state* s) { return s ? s->err.c_str() : ""; }
 
-/* Wall-normal reconstruction and donor selection, Sect. 2.3
+/* Wall-normal reconstruction and donor selection, Sect. 2.2
  * (Eqs. local_wall_normal .. donor_to_solid). Integer form: m_q = 6 w_q. */
 int orc_set_geometry(orc_state* s, const uint8_t* solid) {
   if (!s || !solid) return -1;
@@ -546,7 +546,7 @@ int orc_set_mass_ref(orc_state* s, double m) {
   return 0;
 }
 
-/* Sect. 2.3, Algorithm 1: every ghost from the current field, then assign. */
+/* Sect. 2.2, Algorithm 1: every ghost from the current field, then assign. */
 int orc_ghost_update(orc_state* s) {
   if (!s || !s->has_fields) return -1;
   const long W = (long)s->w_idx.size();
@@ -596,7 +596,7 @@ int orc_lb_collide(orc_state* s) {
   return 0;
 }
 
-/* Sect. 2.2, Eq. phi_update_muscl at fluid nodes; phi* replaces phi. The
+/* Sect. 2.1.1, Eq. phi_update_muscl at fluid nodes; phi* replaces phi. The
  * limited slopes s^d (Eq. slope_minmod_x) and the compressive vector field a
  * are node fields; they are formed first, then differenced. */
 int orc_phase_update(orc_state* s) {
@@ -661,7 +661,7 @@ int orc_phase_update(orc_state* s) {
   return 0;
 }
 
-/* Sect. 2.4, Eqs. tentative_phase_field_mass .. mass_corrected_phi. */
+/* Sect. 2.3, Eqs. tentative_phase_field_mass .. mass_corrected_phi. */
 int orc_volume_correct(orc_state* s) {
   if (!s || !s->has_fields) return -1;
   const long N = s->N;

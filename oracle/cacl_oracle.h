@@ -26,7 +26,7 @@ typedef struct {
   int dim;            /* 3 -> D3Q27, 2 -> D2Q9 (then nz must be 1) */
   int nx, ny, nz;
   int periodic[3];    /* non-periodic axes must be closed by solid layers */
-  double width;       /* interface width delta (Sect. 2.2, Eq. kappa_delta) */
+  double width;       /* interface width delta (Sect. 2.1.1, Eq. kappa_delta) */
   double mobility;    /* interface diffusivity D */
   double sigma;       /* surface tension */
   double rho_l, rho_g;

@@ -158,19 +158,32 @@ def volume_correct_noalloc(phi, solid, m_ref, eps_phi=1e-3, out=None,
                            stream=None):
     """Allocation-free volume correction of a phase field held in torch
     CUDA tensors: ``phi`` (float32, corrected in place), ``solid`` (uint8,
-    nonzero = solid), ``out`` (float64, 3 values: M*, W, lambda) or None.
-    Enqueued on ``stream`` (default: torch's current stream)."""
+    nonzero = solid), ``out`` (float64, at least 3 values: M*, W, lambda) or
+    None. All tensors must be contiguous and on one CUDA device; the call
+    runs with that device current, enqueued on ``stream`` (default: that
+    device's current torch stream)."""
+    import torch
     L = load()
-    if not (phi.is_cuda and solid.is_cuda and phi.is_contiguous()
-            and solid.is_contiguous()):
-        raise ValueError("phi and solid must be contiguous CUDA tensors")
+    tens = [("phi", phi, torch.float32), ("solid", solid, torch.uint8)]
+    if out is not None:
+        tens.append(("out", out, torch.float64))
+    for name, t, dt in tens:
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if t.device != phi.device:
+            raise ValueError(f"{name} is on {t.device}, phi on {phi.device}")
     if phi.numel() != solid.numel():
         raise ValueError("phi and solid differ in size")
-    s = current_stream() if stream is None else stream
-    rc = L.cacl_volume_correct_noalloc(
-        C.c_void_p(phi.data_ptr()), C.c_void_p(solid.data_ptr()),
-        int(phi.numel()), float(m_ref), float(eps_phi),
-        None if out is None else C.c_void_p(out.data_ptr()), C.c_void_p(s))
+    if out is not None and out.numel() < 3:
+        raise ValueError("out must hold at least 3 doubles")
+    with torch.cuda.device(phi.device):
+        s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        rc = L.cacl_volume_correct_noalloc(
+            C.c_void_p(phi.data_ptr()), C.c_void_p(solid.data_ptr()),
+            int(phi.numel()), float(m_ref), float(eps_phi),
+            None if out is None else C.c_void_p(out.data_ptr()), C.c_void_p(s))
     if rc != CACL_OK:
         raise CaclError(rc, "cacl_volume_correct_noalloc")
 

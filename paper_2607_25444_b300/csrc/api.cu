@@ -37,7 +37,7 @@ void drop_graphs(cacl_ctx* c) {
 }
 
 // cot(theta_c), theta_c = pi - theta (Eq. internal_contact_angle), with the
-// regularisation near |sin theta_c| -> 0 (Sect. 2.3).
+// regularisation near |sin theta_c| -> 0 (Sect. 2.2).
 double cot_internal(double theta_deg) {
   const double thc = kPi - theta_deg * kPi / 180.0;
   const double s = std::sin(thc), co = std::cos(thc);
@@ -161,6 +161,7 @@ cacl_status cacl_create(const cacl_params* p, void* stream, cacl_ctx** out) {
   if ((e = cudaMalloc(&c->a, sizeof(float) * 3 * N)) != cudaSuccess)
     return bail("alloc a");
   if ((e = cudaMalloc(&c->flags, N)) != cudaSuccess) return bail("alloc flags");
+  if ((e = lb_tma_init(c)) != cudaSuccess) return bail("collide-stream tensor maps");
   c->part_blocks = phase_blocks(c);
   const int pb = std::max(c->part_blocks, mass_ref_blocks(N));
   if ((e = cudaMalloc(&c->partials, sizeof(double) * 2 * pb)) != cudaSuccess)
@@ -496,7 +497,7 @@ cacl_status cacl_set_option(cacl_ctx* c, int option, int value) {
     return CACL_OK;
   }
   if (option == CACL_OPT_LB_PIPE) {
-    if (value < 0 || value > 1) return fail(c, CACL_ERR_ARG, "unknown collide pipeline");
+    if (value < 0 || value > 3) return fail(c, CACL_ERR_ARG, "unknown collide pipeline");
     const int pf = 16 / (int)storage_bytes(c->p.storage);
     if (value == 1 && (c->g.nx % pf != 0 || c->g.nx % 4 != 0))
       return fail(c, CACL_ERR_ARG, "staged collide-stream needs nx a multiple of 16 bytes");

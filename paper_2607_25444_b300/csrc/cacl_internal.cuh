@@ -6,6 +6,7 @@
 // (Sect. 2.1), c_s^2 = 1/3. Everything is derived from q at compile time.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -44,15 +45,24 @@ __host__ __device__ constexpr float wq(int q) {
 // stores the population w_q P given P = f_q / w_q.
 struct StoreF32 {
   using T = float;
+  using T2 = float2;  // two x-adjacent nodes
   __device__ __forceinline__ static float decode(T v, int q) { return v; }
   __device__ __forceinline__ static T encode(float v, int q) { return v; }
   __device__ __forceinline__ static T encode_w(float P, int q) { return wq(q) * P; }
+  __device__ __forceinline__ static float2 decode2(T2 v, int q) { return v; }
+  __device__ __forceinline__ static T2 encode_w2(float2 P, int q) {
+    return __fmul2_rn(make_float2(wq(q), wq(q)), P);
+  }
+  __device__ __forceinline__ static T2 pack(T lo, T hi) { return make_float2(lo, hi); }
+  __device__ __forceinline__ static T lo(T2 v) { return v.x; }
+  __device__ __forceinline__ static T hi(T2 v) { return v.y; }
 };
 
 struct StoreF16 {
   using T = __half;
+  using T2 = __half2;
   __device__ __forceinline__ static float decode(T v, int q) {
-    return __half2float(v) * wq(q);
+    return __fmul_rn(__half2float(v), wq(q));
   }
   __device__ __forceinline__ static T encode(float v, int q) {
     return __float2half_rn(v * (1.0f / wq(q)));
@@ -60,12 +70,23 @@ struct StoreF16 {
   __device__ __forceinline__ static T encode_w(float P, int q) {
     return __float2half_rn(P);
   }
+  __device__ __forceinline__ static float2 decode2(T2 v, int q) {
+    const float2 h = __half22float2(v);
+    return make_float2(__fmul_rn(h.x, wq(q)), __fmul_rn(h.y, wq(q)));
+  }
+  __device__ __forceinline__ static T2 encode_w2(float2 P, int q) {
+    return __float22half2_rn(P);
+  }
+  __device__ __forceinline__ static T2 pack(T lo, T hi) { return __halves2half2(lo, hi); }
+  __device__ __forceinline__ static T lo(T2 v) { return __low2half(v); }
+  __device__ __forceinline__ static T hi(T2 v) { return __high2half(v); }
 };
 
 struct StoreBF16 {
   using T = __nv_bfloat16;
+  using T2 = __nv_bfloat162;
   __device__ __forceinline__ static float decode(T v, int q) {
-    return __bfloat162float(v) * wq(q);
+    return __fmul_rn(__bfloat162float(v), wq(q));
   }
   __device__ __forceinline__ static T encode(float v, int q) {
     return __float2bfloat16_rn(v * (1.0f / wq(q)));
@@ -73,6 +94,18 @@ struct StoreBF16 {
   __device__ __forceinline__ static T encode_w(float P, int q) {
     return __float2bfloat16_rn(P);
   }
+  __device__ __forceinline__ static float2 decode2(T2 v, int q) {
+    const float2 h = __bfloat1622float2(v);
+    return make_float2(__fmul_rn(h.x, wq(q)), __fmul_rn(h.y, wq(q)));
+  }
+  __device__ __forceinline__ static T2 encode_w2(float2 P, int q) {
+    return __float22bfloat162_rn(P);
+  }
+  __device__ __forceinline__ static T2 pack(T lo, T hi) {
+    return __halves2bfloat162(lo, hi);
+  }
+  __device__ __forceinline__ static T lo(T2 v) { return __low2bfloat16(v); }
+  __device__ __forceinline__ static T hi(T2 v) { return __high2bfloat16(v); }
 };
 
 inline size_t storage_bytes(int storage) { return storage == CACL_F32 ? 4 : 2; }
@@ -95,19 +128,46 @@ __device__ __forceinline__ int wrap(int i, int d, int n) {
   return (j >= n) ? j - n : j;
 }
 
+// Arithmetic on one node (float) or on a pair of x-adjacent nodes (float2,
+// the packed FP32 pair operations of sm_100 and later). Every operation is
+// round-to-nearest and is never contracted, and a pair operation rounds
+// each lane exactly as the scalar operation does, so a kernel that handles
+// two nodes per thread gives the same bits as one that handles one.
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
+  return __ffma2_rn(a, b, c);
+}
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fadd_rn(a, -b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, vneg(b)); }
+// 1 / a, correctly rounded, per lane
+__device__ __forceinline__ float vrcp(float a) { return 1.0f / a; }
+__device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(1.0f / a.x, 1.0f / a.y); }
+template <typename V> __device__ __forceinline__ V splat(float c);
+template <> __device__ __forceinline__ float splat<float>(float c) { return c; }
+template <> __device__ __forceinline__ float2 splat<float2>(float c) {
+  return make_float2(c, c);
+}
+
 // One pair of opposite links (q, 26 - q) of the isotropic phi stencil (Eqs.
 // grad_iso, lap_iso): phi at x + c_q (vp) and x - c_q (vm) added to the
 // gradient and to sum_q w_q phi(x + c_q), in explicitly rounded operations.
-__device__ __forceinline__ void stencil_pair(int q, float vp, float vm, float& gx,
-                                             float& gy, float& gz, float& ssum) {
-  const float dv = __fmul_rn(3.0f * wq(q), __fadd_rn(vp, -vm));
-  if (cx(q) > 0) gx = __fadd_rn(gx, dv);
-  if (cx(q) < 0) gx = __fadd_rn(gx, -dv);
-  if (cy(q) > 0) gy = __fadd_rn(gy, dv);
-  if (cy(q) < 0) gy = __fadd_rn(gy, -dv);
-  if (cz(q) > 0) gz = __fadd_rn(gz, dv);
-  if (cz(q) < 0) gz = __fadd_rn(gz, -dv);
-  ssum = fmaf(wq(q), __fadd_rn(vp, vm), ssum);
+template <typename V>
+__device__ __forceinline__ void stencil_pair(int q, V vp, V vm, V& gx, V& gy, V& gz,
+                                             V& ssum) {
+  const V dv = vmul(splat<V>(3.0f * wq(q)), vadd(vp, vneg(vm)));
+  if (cx(q) > 0) gx = vadd(gx, dv);
+  if (cx(q) < 0) gx = vadd(gx, vneg(dv));
+  if (cy(q) > 0) gy = vadd(gy, dv);
+  if (cy(q) < 0) gy = vadd(gy, vneg(dv));
+  if (cz(q) > 0) gz = vadd(gz, dv);
+  if (cz(q) < 0) gz = vadd(gz, vneg(dv));
+  ssum = vfma(splat<V>(wq(q)), vadd(vp, vm), ssum);
 }
 
 // Isotropic gradient (Eq. grad_iso) and the neighbour sum of Eq. lap_iso of
@@ -131,7 +191,7 @@ __device__ __forceinline__ void phi_stencil(const float* __restrict__ phi,
   }
 }
 
-// Compressive vector a = phi (1 - phi) grad phi / |grad phi| (Sect. 2.2),
+// Compressive vector a = phi (1 - phi) grad phi / |grad phi| (Sect. 2.1.1),
 // zero where |grad phi| < 1e-12.
 __device__ __forceinline__ void compressive(float phi0, float gx, float gy,
                                             float gz, float& ax, float& ay,
@@ -144,6 +204,14 @@ __device__ __forceinline__ void compressive(float phi0, float gx, float gy,
     ay = __fmul_rn(sc, gy);
     az = __fmul_rn(sc, gz);
   }
+}
+
+// The same for a pair of nodes, lane by lane.
+__device__ __forceinline__ void compressive(float2 phi0, float2 gx, float2 gy,
+                                            float2 gz, float2& ax, float2& ay,
+                                            float2& az) {
+  compressive(phi0.x, gx.x, gy.x, gz.x, ax.x, ay.x, az.x);
+  compressive(phi0.y, gx.y, gy.y, gz.y, ax.y, ay.y, az.y);
 }
 
 // Scalar parameters uploaded once per context.
@@ -339,8 +407,15 @@ struct cacl_ctx {
   // kernel shape choices (cacl_set_option)
   int phase_variant = 2;
   int phase_pipe = 0;      // 0 auto, 1 register staging, 2 cp.async staging
-  int lb_pipe = 0;         // 0 direct loads, 1 bulk-copy staged rows
+  int lb_pipe = 0;         // 0 two nodes per thread (else one), 1 bulk-copy
+                           // staged rows, 2 one node per thread, 3 TMA-tiled
+                           // (else two nodes per thread)
   int lb_grid = 1;         // blocks of the persistent staged collide-stream
+  // tensor maps of the TMA-tiled collide-stream (nx a multiple of 8):
+  // population loads and stores per buffer, phi loads per buffer, u and a
+  // stores; valid when lbt_ok
+  bool lbt_ok = false;
+  CUtensorMap lbt_fload[2], lbt_fstore[2], lbt_phi[2], lbt_u, lbt_a;
   int phase_nblocks = 0;   // blocks of the last phase-update launch
 
   // reductions
@@ -367,6 +442,11 @@ cudaError_t launch_ghost(cacl_ctx* c, float* phi);
 cudaError_t lb_init(cacl_ctx* c);
 bool lb_staged_ok(const cacl_ctx* c, const void* fin, const void* fout,
                   const void* phi);
+bool lb_pair_ok(const cacl_ctx* c, const void* fin, const void* fout,
+                const void* phi);
+cudaError_t lb_tma_init(cacl_ctx* c);
+bool lb_tma_ok(const cacl_ctx* c, const void* fin, const void* fout,
+               const void* phi);
 cudaError_t launch_lb(cacl_ctx* c, const void* fin, void* fout,
                       const float* phi);
 cudaError_t launch_compressive(cacl_ctx* c, const float* phi);

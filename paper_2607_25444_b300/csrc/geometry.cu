@@ -1,4 +1,4 @@
-// geometry.cu -- node flags and the wall list (Sect. 2.3,
+// geometry.cu -- node flags and the wall list (Sect. 2.2,
 // Eqs. local_wall_normal, wall_normal_weights, unit_wall_normal,
 // donor_alignment_score, donor_selection, donor_to_solid).
 //

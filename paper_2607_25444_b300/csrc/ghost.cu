@@ -1,4 +1,4 @@
-// ghost.cu -- ghost phi values at wall nodes (Sect. 2.3, Algorithm 1,
+// ghost.cu -- ghost phi values at wall nodes (Sect. 2.2, Algorithm 1,
 // Eqs. tangential_gradient_contact_angle .. contact_angle_localization).
 //
 // Jacobi semantics: ghost_eval computes every ghost from phi^n into a

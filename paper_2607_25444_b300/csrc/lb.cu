@@ -8,7 +8,7 @@
 // when x - c_q is solid), the phi stencil is read through the read-only
 // cache, and the node writes its 27 post-collision populations, u, and the
 // compressive vector a = phi (1 - phi) grad phi / |grad phi| of the same
-// phi^n, which the phi update of this step needs at every node (Sect. 2.2):
+// phi^n, which the phi update of this step needs at every node (Sect. 2.1.1):
 // the gradient is already in registers here.
 //
 // Collision algebra. With A2 = Pi - p* c_s^2 I - u u + (u a + a u)/2 (the
@@ -37,6 +37,8 @@
 // operations instead of a separate polynomial per direction pair. The
 // moments are formed the same way in reverse (sums and differences along x,
 // then y, then z).
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 
 #include "cacl_internal.cuh"
@@ -46,176 +48,216 @@ namespace {
 
 constexpr int LB_BX = 128;
 constexpr int LB_BY = 1;
+// two-node (x pair) kernel: PX pairs along x times PY rows per block
+constexpr int LB2_PX = 32;
+constexpr int LB2_PY = 4;
 
+// Post-collision state of one node (V = float) or of an x pair of nodes
+// (V = float2, both lanes rounded exactly as the one-node form).
+template <typename V>
 struct NodeOut {
-  float P[Q];  // f*_q / w_q
-  float ux, uy, uz;
+  V P[Q];  // f*_q / w_q
+  V ux, uy, uz;
 };
 
-__device__ __forceinline__ void collide(const float (&f)[Q], float phi0,
-                                        float gx, float gy, float gz, float lap,
-                                        const Consts& k, NodeOut& o) {
+template <typename V>
+__device__ __forceinline__ void collide(const V (&f)[Q], V phi0, V gx, V gy,
+                                        V gz, V lap, const Consts& k,
+                                        NodeOut<V>& o) {
   // moments by sum factorisation: along x for each (cy, cz) line l, then
   // along y for each cz, then along z (q = 9 (cz+1) + 3 (cy+1) + (cx+1))
-  float m0[9], m1[9], m2[9];  // sum f, sum cx f, sum cx^2 f over the line
+  V m0[9], m1[9], m2[9];  // sum f, sum cx f, sum cx^2 f over the line
 #pragma unroll
   for (int l = 0; l < 9; ++l) {
-    m2[l] = f[3 * l + 2] + f[3 * l];
-    m1[l] = f[3 * l + 2] - f[3 * l];
-    m0[l] = m2[l] + f[3 * l + 1];
+    m2[l] = vadd(f[3 * l + 2], f[3 * l]);
+    m1[l] = vsub(f[3 * l + 2], f[3 * l]);
+    m0[l] = vadd(m2[l], f[3 * l + 1]);
   }
-  float n00[3], n01[3], n02[3], n10[3], n11[3], n20[3];
+  V n00[3], n01[3], n02[3], n10[3], n11[3], n20[3];
 #pragma unroll
   for (int kz = 0; kz < 3; ++kz) {
     const int l = 3 * kz;  // lines cy = -1, 0, 1 at l, l+1, l+2
-    n02[kz] = m0[l + 2] + m0[l];      // sum cy^2 f
-    n01[kz] = m0[l + 2] - m0[l];      // sum cy f
-    n00[kz] = n02[kz] + m0[l + 1];    // sum f
-    n11[kz] = m1[l + 2] - m1[l];      // sum cx cy f
-    n10[kz] = (m1[l + 2] + m1[l]) + m1[l + 1];  // sum cx f
-    n20[kz] = (m2[l + 2] + m2[l]) + m2[l + 1];  // sum cx^2 f
+    n02[kz] = vadd(m0[l + 2], m0[l]);      // sum cy^2 f
+    n01[kz] = vsub(m0[l + 2], m0[l]);      // sum cy f
+    n00[kz] = vadd(n02[kz], m0[l + 1]);    // sum f
+    n11[kz] = vsub(m1[l + 2], m1[l]);      // sum cx cy f
+    n10[kz] = vadd(vadd(m1[l + 2], m1[l]), m1[l + 1]);  // sum cx f
+    n20[kz] = vadd(vadd(m2[l + 2], m2[l]), m2[l + 1]);  // sum cx^2 f
   }
-  const float Pzz = n00[2] + n00[0];
-  const float p = Pzz + n00[1];
-  const float jz = n00[2] - n00[0];
-  const float jy = (n01[2] + n01[0]) + n01[1];
-  const float Pyz = n01[2] - n01[0];
-  const float Pyy = (n02[2] + n02[0]) + n02[1];
-  const float jx = (n10[2] + n10[0]) + n10[1];
-  const float Pxz = n10[2] - n10[0];
-  const float Pxy = (n11[2] + n11[0]) + n11[1];
-  const float Pxx = (n20[2] + n20[0]) + n20[1];
+  const V Pzz = vadd(n00[2], n00[0]);
+  const V p = vadd(Pzz, n00[1]);
+  const V jz = vsub(n00[2], n00[0]);
+  const V jy = vadd(vadd(n01[2], n01[0]), n01[1]);
+  const V Pyz = vsub(n01[2], n01[0]);
+  const V Pyy = vadd(vadd(n02[2], n02[0]), n02[1]);
+  const V jx = vadd(vadd(n10[2], n10[0]), n10[1]);
+  const V Pxz = vsub(n10[2], n10[0]);
+  const V Pxy = vadd(vadd(n11[2], n11[0]), n11[1]);
+  const V Pxx = vadd(vadd(n20[2], n20[0]), n20[1]);
 
   // Every product and sum below is an explicit round-to-nearest operation
-  // (fmaf, or __fmul_rn / __fadd_rn, which are never contracted), so that
-  // each kernel that inlines the collision rounds it the same way.
-  const float rho = fmaf(k.drho, phi0, k.rho_g);
-  const float mu = fmaf(k.dmu, phi0, k.mu_g);
-  const float inv_rho = 1.0f / rho;
-  const float nu = __fmul_rn(mu, inv_rho);
-  const float omega = 1.0f / fmaf(3.0f, nu, 0.5f);
-  const float grx = __fmul_rn(k.drho, gx), gry = __fmul_rn(k.drho, gy),
-              grz = __fmul_rn(k.drho, gz);
-  const float muphi = fmaf(-k.kappa_phi, lap,
-                           __fmul_rn(__fmul_rn(__fmul_rn(k.beta4, phi0),
-                                               __fadd_rn(phi0, -1.0f)),
-                                     __fadd_rn(phi0, -0.5f)));
-  const float p3 = __fmul_rn(p, 1.0f / 3.0f);
-  const float rb = __fadd_rn(rho, -k.rho_g);
-  const float F0x = fmaf(rb, k.gx, fmaf(-p3, grx, __fmul_rn(muphi, gx)));
-  const float F0y = fmaf(rb, k.gy, fmaf(-p3, gry, __fmul_rn(muphi, gy)));
-  const float F0z = fmaf(rb, k.gz, fmaf(-p3, grz, __fmul_rn(muphi, gz)));
+  // (vfma / vmul / vadd, never contracted), so that each kernel that
+  // inlines the collision rounds it the same way.
+  auto C = [](float c) { return splat<V>(c); };
+  const V rho = vfma(C(k.drho), phi0, C(k.rho_g));
+  const V mu = vfma(C(k.dmu), phi0, C(k.mu_g));
+  const V inv_rho = vrcp(rho);
+  const V nu = vmul(mu, inv_rho);
+  const V omega = vrcp(vfma(C(3.0f), nu, C(0.5f)));
+  const V grx = vmul(C(k.drho), gx), gry = vmul(C(k.drho), gy),
+          grz = vmul(C(k.drho), gz);
+  const V muphi = vfma(C(-k.kappa_phi), lap,
+                       vmul(vmul(vmul(C(k.beta4), phi0), vadd(phi0, C(-1.0f))),
+                            vadd(phi0, C(-0.5f))));
+  const V p3 = vmul(p, C(1.0f / 3.0f));
+  const V rb = vadd(rho, C(-k.rho_g));
+  const V F0x = vfma(rb, C(k.gx), vfma(vneg(p3), grx, vmul(muphi, gx)));
+  const V F0y = vfma(rb, C(k.gy), vfma(vneg(p3), gry, vmul(muphi, gy)));
+  const V F0z = vfma(rb, C(k.gz), vfma(vneg(p3), grz, vmul(muphi, gz)));
   // predictor for the viscous correction (Eq. Fnu)
-  const float a0x = __fmul_rn(F0x, inv_rho), a0y = __fmul_rn(F0y, inv_rho),
-              a0z = __fmul_rn(F0z, inv_rho);
-  const float u0x = fmaf(0.5f, a0x, jx), u0y = fmaf(0.5f, a0y, jy),
-              u0z = fmaf(0.5f, a0z, jz);
+  const V a0x = vmul(F0x, inv_rho), a0y = vmul(F0y, inv_rho),
+          a0z = vmul(F0z, inv_rho);
+  const V u0x = vfma(C(0.5f), a0x, jx), u0y = vfma(C(0.5f), a0y, jy),
+          u0z = vfma(C(0.5f), a0z, jz);
   // Q0 = Pi - p* c_s^2 I - u0 u0 + (u0 a0 + a0 u0) / 2
-  auto qd = [](float P, float p3_, float uu_, float aa_) {
-    return fmaf(uu_, __fadd_rn(aa_, -uu_), __fadd_rn(P, -p3_));
+  auto qd = [](V P, V p3_, V uu_, V aa_) {
+    return vfma(uu_, vadd(aa_, vneg(uu_)), vadd(P, vneg(p3_)));
   };
-  auto qo = [](float P, float ua, float ub, float aa, float ab) {
-    return fmaf(0.5f, fmaf(ua, ab, __fmul_rn(aa, ub)), fmaf(-ua, ub, P));
+  auto qo = [](V P, V ua, V ub, V aa, V ab) {
+    return vfma(splat<V>(0.5f), vfma(ua, ab, vmul(aa, ub)), vfma(vneg(ua), ub, P));
   };
-  const float Q0xx = qd(Pxx, p3, u0x, a0x);
-  const float Q0yy = qd(Pyy, p3, u0y, a0y);
-  const float Q0zz = qd(Pzz, p3, u0z, a0z);
-  const float Q0xy = qo(Pxy, u0x, u0y, a0x, a0y);
-  const float Q0xz = qo(Pxz, u0x, u0z, a0x, a0z);
-  const float Q0yz = qo(Pyz, u0y, u0z, a0y, a0z);
-  const float cnu = __fmul_rn(__fmul_rn(-3.0f, nu), omega);
-  auto dot3 = [](float a1, float b1, float a2, float b2, float a3, float b3) {
-    return fmaf(a3, b3, fmaf(a2, b2, __fmul_rn(a1, b1)));
+  const V Q0xx = qd(Pxx, p3, u0x, a0x);
+  const V Q0yy = qd(Pyy, p3, u0y, a0y);
+  const V Q0zz = qd(Pzz, p3, u0z, a0z);
+  const V Q0xy = qo(Pxy, u0x, u0y, a0x, a0y);
+  const V Q0xz = qo(Pxz, u0x, u0z, a0x, a0z);
+  const V Q0yz = qo(Pyz, u0y, u0z, a0y, a0z);
+  const V cnu = vmul(vmul(C(-3.0f), nu), omega);
+  auto dot3 = [](V a1, V b1, V a2, V b2, V a3, V b3) {
+    return vfma(a3, b3, vfma(a2, b2, vmul(a1, b1)));
   };
-  const float Fx = fmaf(cnu, dot3(Q0xx, grx, Q0xy, gry, Q0xz, grz), F0x);
-  const float Fy = fmaf(cnu, dot3(Q0xy, grx, Q0yy, gry, Q0yz, grz), F0y);
-  const float Fz = fmaf(cnu, dot3(Q0xz, grx, Q0yz, gry, Q0zz, grz), F0z);
-  const float ax = __fmul_rn(Fx, inv_rho), ay = __fmul_rn(Fy, inv_rho),
-              az = __fmul_rn(Fz, inv_rho);
-  const float ux = fmaf(0.5f, ax, jx), uy = fmaf(0.5f, ay, jy), uz = fmaf(0.5f, az, jz);
-  const float Axx = qd(Pxx, p3, ux, ax);
-  const float Ayy = qd(Pyy, p3, uy, ay);
-  const float Azz = qd(Pzz, p3, uz, az);
-  const float Axy = qo(Pxy, ux, uy, ax, ay);
-  const float Axz = qo(Pxz, ux, uz, ax, az);
-  const float Ayz = qo(Pyz, uy, uz, ay, az);
-  const float tr = __fadd_rn(__fadd_rn(Axx, Ayy), Azz);
-  const float vx = dot3(Axx, ux, Axy, uy, Axz, uz);
-  const float vy = dot3(Axy, ux, Ayy, uy, Ayz, uz);
-  const float vz = dot3(Axz, ux, Ayz, uy, Azz, uz);
-  const float uu = dot3(ux, ux, uy, uy, uz, uz);
-  const float ua = dot3(ux, ax, uy, ay, uz, az);
-  const float om45 = __fmul_rn(4.5f, __fadd_rn(1.0f, -omega));
-  const float k1 = fmaf(-__fmul_rn(om45, tr), 1.0f / 3.0f,
-                        fmaf(-1.5f, __fadd_rn(uu, ua), p));
-  const float k2 = fmaf(-om45, tr, fmaf(-4.5f, uu, 3.0f));
+  const V Fx = vfma(cnu, dot3(Q0xx, grx, Q0xy, gry, Q0xz, grz), F0x);
+  const V Fy = vfma(cnu, dot3(Q0xy, grx, Q0yy, gry, Q0yz, grz), F0y);
+  const V Fz = vfma(cnu, dot3(Q0xz, grx, Q0yz, gry, Q0zz, grz), F0z);
+  const V ax = vmul(Fx, inv_rho), ay = vmul(Fy, inv_rho), az = vmul(Fz, inv_rho);
+  const V ux = vfma(C(0.5f), ax, jx), uy = vfma(C(0.5f), ay, jy),
+          uz = vfma(C(0.5f), az, jz);
+  const V Axx = qd(Pxx, p3, ux, ax);
+  const V Ayy = qd(Pyy, p3, uy, ay);
+  const V Azz = qd(Pzz, p3, uz, az);
+  const V Axy = qo(Pxy, ux, uy, ax, ay);
+  const V Axz = qo(Pxz, ux, uz, ax, az);
+  const V Ayz = qo(Pyz, uy, uz, ay, az);
+  const V tr = vadd(vadd(Axx, Ayy), Azz);
+  const V vx = dot3(Axx, ux, Axy, uy, Axz, uz);
+  const V vy = dot3(Axy, ux, Ayy, uy, Ayz, uz);
+  const V vz = dot3(Axz, ux, Ayz, uy, Azz, uz);
+  const V uu = dot3(ux, ux, uy, uy, uz, uz);
+  const V ua = dot3(ux, ax, uy, ay, uz, az);
+  const V om45 = vmul(C(4.5f), vadd(C(1.0f), vneg(omega)));
+  const V k1 = vfma(vneg(vmul(om45, tr)), C(1.0f / 3.0f),
+                    vfma(C(-1.5f), vadd(uu, ua), p));
+  const V k2 = vfma(vneg(om45), tr, vfma(C(-4.5f), uu, C(3.0f)));
 
   // coefficients of P in the separable monomials
-  const float om3 = __fmul_rn(3.0f, om45), om6 = __fmul_rn(6.0f, om45),
-              om2 = __fmul_rn(2.0f, om45);
-  auto coefD = [&](float u_, float a_, float A_) {
-    return fmaf(om45, A_, __fmul_rn(__fmul_rn(4.5f, u_), __fadd_rn(u_, a_)));
+  const V om3 = vmul(C(3.0f), om45), om6 = vmul(C(6.0f), om45),
+          om2 = vmul(C(2.0f), om45);
+  auto coefD = [&](V u_, V a_, V A_) {
+    return vfma(om45, A_, vmul(vmul(C(4.5f), u_), vadd(u_, a_)));
   };
-  auto coefG = [&](float u_, float A_) {
-    return fmaf(om3, A_, __fmul_rn(__fmul_rn(13.5f, u_), u_));
+  auto coefG = [&](V u_, V A_) {
+    return vfma(om3, A_, vmul(vmul(C(13.5f), u_), u_));
   };
-  auto coefL = [&](float u_, float a_, float A_, float v_) {
-    const float in = fmaf(om3, A_, fmaf(__fmul_rn(4.5f, u_), u_, k2));
-    return fmaf(1.5f, a_, fmaf(-om2, v_, __fmul_rn(u_, in)));
+  auto coefL = [&](V u_, V a_, V A_, V v_) {
+    const V in = vfma(om3, A_, vfma(vmul(C(4.5f), u_), u_, k2));
+    return vfma(C(1.5f), a_, vfma(vneg(om2), v_, vmul(u_, in)));
   };
-  auto coefF = [&](float ua_, float ub_, float aa_, float ab_, float A_) {
-    return fmaf(4.5f, fmaf(ua_, ab_, __fmul_rn(ub_, aa_)),
-                fmaf(om2, A_, __fmul_rn(__fmul_rn(9.0f, ua_), ub_)));
+  auto coefF = [&](V ua_, V ub_, V aa_, V ab_, V A_) {
+    return vfma(C(4.5f), vfma(ua_, ab_, vmul(ub_, aa_)),
+                vfma(om2, A_, vmul(vmul(C(9.0f), ua_), ub_)));
   };
-  const float Dx = coefD(ux, ax, Axx), Dy = coefD(uy, ay, Ayy), Dz = coefD(uz, az, Azz);
-  const float Gx = coefG(ux, Axx), Gy = coefG(uy, Ayy), Gz = coefG(uz, Azz);
-  const float Lx = coefL(ux, ax, Axx, vx);
-  const float Ly = coefL(uy, ay, Ayy, vy);
-  const float Lz = coefL(uz, az, Azz, vz);
-  const float Fxy = coefF(ux, uy, ax, ay, Axy);
-  const float Fxz = coefF(ux, uz, ax, az, Axz);
-  const float Fyz = coefF(uy, uz, ay, az, Ayz);
-  const float Hxy = __fmul_rn(om6, Axy), Hxz = __fmul_rn(om6, Axz),
-              Hyz = __fmul_rn(om6, Ayz);
-  const float Mxy = fmaf(ux, Hxy, __fmul_rn(uy, Gx));  // e_x c_y
-  const float Mxz = fmaf(ux, Hxz, __fmul_rn(uz, Gx));  // e_x c_z
-  const float Myx = fmaf(uy, Hxy, __fmul_rn(ux, Gy));  // e_y c_x
-  const float Myz = fmaf(uy, Hyz, __fmul_rn(uz, Gy));  // e_y c_z
-  const float Mzx = fmaf(uz, Hxz, __fmul_rn(ux, Gz));  // e_z c_x
-  const float Mzy = fmaf(uz, Hyz, __fmul_rn(uy, Gz));  // e_z c_y
-  const float X = fmaf(om6, dot3(ux, Ayz, uy, Axz, uz, Axy),
-                       __fmul_rn(__fmul_rn(__fmul_rn(27.0f, ux), uy), uz));
+  const V Dx = coefD(ux, ax, Axx), Dy = coefD(uy, ay, Ayy), Dz = coefD(uz, az, Azz);
+  const V Gx = coefG(ux, Axx), Gy = coefG(uy, Ayy), Gz = coefG(uz, Azz);
+  const V Lx = coefL(ux, ax, Axx, vx);
+  const V Ly = coefL(uy, ay, Ayy, vy);
+  const V Lz = coefL(uz, az, Azz, vz);
+  const V Fxy = coefF(ux, uy, ax, ay, Axy);
+  const V Fxz = coefF(ux, uz, ax, az, Axz);
+  const V Fyz = coefF(uy, uz, ay, az, Ayz);
+  const V Hxy = vmul(om6, Axy), Hxz = vmul(om6, Axz), Hyz = vmul(om6, Ayz);
+  const V Mxy = vfma(ux, Hxy, vmul(uy, Gx));  // e_x c_y
+  const V Mxz = vfma(ux, Hxz, vmul(uz, Gx));  // e_x c_z
+  const V Myx = vfma(uy, Hxy, vmul(ux, Gy));  // e_y c_x
+  const V Myz = vfma(uy, Hyz, vmul(uz, Gy));  // e_y c_z
+  const V Mzx = vfma(uz, Hxz, vmul(ux, Gz));  // e_z c_x
+  const V Mzy = vfma(uz, Hyz, vmul(uy, Gz));  // e_z c_y
+  const V X = vfma(om6, dot3(ux, Ayz, uy, Axz, uz, Axy),
+                   vmul(vmul(vmul(C(27.0f), ux), uy), uz));
 
   // z transform: Z_ij(cz) for x basis i, y basis j (1, c, e); index cz+1
-  float Z00[3], Z10[3], Z20[3], Z01[3], Z11[3], Z02[3];
+  V Z00[3], Z10[3], Z20[3], Z01[3], Z11[3], Z02[3];
   {
-    const float t00 = k1 + Dz, t10 = Lx + Mzx, t01 = Ly + Mzy;
-    Z00[0] = t00 - Lz; Z00[1] = k1; Z00[2] = t00 + Lz;
-    Z10[0] = t10 - Fxz; Z10[1] = Lx; Z10[2] = t10 + Fxz;
-    Z20[0] = Dx - Mxz; Z20[1] = Dx; Z20[2] = Dx + Mxz;
-    Z01[0] = t01 - Fyz; Z01[1] = Ly; Z01[2] = t01 + Fyz;
-    Z11[0] = Fxy - X; Z11[1] = Fxy; Z11[2] = Fxy + X;
-    Z02[0] = Dy - Myz; Z02[1] = Dy; Z02[2] = Dy + Myz;
+    const V t00 = vadd(k1, Dz), t10 = vadd(Lx, Mzx), t01 = vadd(Ly, Mzy);
+    Z00[0] = vsub(t00, Lz); Z00[1] = k1; Z00[2] = vadd(t00, Lz);
+    Z10[0] = vsub(t10, Fxz); Z10[1] = Lx; Z10[2] = vadd(t10, Fxz);
+    Z20[0] = vsub(Dx, Mxz); Z20[1] = Dx; Z20[2] = vadd(Dx, Mxz);
+    Z01[0] = vsub(t01, Fyz); Z01[1] = Ly; Z01[2] = vadd(t01, Fyz);
+    Z11[0] = vsub(Fxy, X); Z11[1] = Fxy; Z11[2] = vadd(Fxy, X);
+    Z02[0] = vsub(Dy, Myz); Z02[1] = Dy; Z02[2] = vadd(Dy, Myz);
   }
   // y transform then x transform, line by line (cy, cz)
 #pragma unroll
   for (int kz = 0; kz < 3; ++kz) {
-    const float t0 = Z00[kz] + Z02[kz], t1 = Z10[kz] + Myx;
-    const float Y0[3] = {t0 - Z01[kz], Z00[kz], t0 + Z01[kz]};
-    const float Y1[3] = {t1 - Z11[kz], Z10[kz], t1 + Z11[kz]};
-    const float Y2[3] = {Z20[kz] - Mxy, Z20[kz], Z20[kz] + Mxy};
+    const V t0 = vadd(Z00[kz], Z02[kz]), t1 = vadd(Z10[kz], Myx);
+    const V Y0[3] = {vsub(t0, Z01[kz]), Z00[kz], vadd(t0, Z01[kz])};
+    const V Y1[3] = {vsub(t1, Z11[kz]), Z10[kz], vadd(t1, Z11[kz])};
+    const V Y2[3] = {vsub(Z20[kz], Mxy), Z20[kz], vadd(Z20[kz], Mxy)};
 #pragma unroll
     for (int jy = 0; jy < 3; ++jy) {
       const int q = 9 * kz + 3 * jy;
-      const float t = Y0[jy] + Y2[jy];
-      o.P[q] = t - Y1[jy];
+      const V t = vadd(Y0[jy], Y2[jy]);
+      o.P[q] = vsub(t, Y1[jy]);
       o.P[q + 1] = Y0[jy];
-      o.P[q + 2] = t + Y1[jy];
+      o.P[q + 2] = vadd(t, Y1[jy]);
     }
   }
   o.ux = ux;
   o.uy = uy;
   o.uz = uz;
+}
+
+// Laplacian of Eq. lap_iso from the neighbour sum: 6 (ssum - (1 - w_0) phi).
+template <typename V>
+__device__ __forceinline__ V lap_from_sum(V phi0, V ssum) {
+  return vmul(splat<V>(6.0f), vfma(splat<V>(-(1.0f - wq(REST))), phi0, ssum));
+}
+
+// Everything after the pull and the phi stencil of one node: the
+// Laplacian, the compressive vector a and the collision.
+template <typename V>
+__device__ __forceinline__ void node_eval(const V (&f)[Q], V phi0, V gx, V gy,
+                                          V gz, V ssum, const Consts& k,
+                                          NodeOut<V>& o, V& ax, V& ay, V& az) {
+  const V lap = lap_from_sum(phi0, ssum);
+  compressive(phi0, gx, gy, gz, ax, ay, az);
+  collide(f, phi0, gx, gy, gz, lap, k, o);
+}
+
+// Stores of one node's f*, u and a.
+template <typename Store, typename IDX>
+__device__ __forceinline__ void node_store(IDX n, IDX N, const NodeOut<float>& o,
+                                           float ax, float ay, float az,
+                                           typename Store::T* __restrict__ fout,
+                                           float* __restrict__ u,
+                                           float* __restrict__ a) {
+  a[n] = ax;
+  a[N + n] = ay;
+  a[2 * N + n] = az;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) fout[q * N + n] = Store::encode_w(o.P[q], q);
+  u[n] = o.ux;
+  u[N + n] = o.uy;
+  u[2 * N + n] = o.uz;
 }
 
 // Everything after the pull and the phi stencil: the compressive vector
@@ -228,40 +270,31 @@ __device__ __forceinline__ void lb_finish(IDX n, IDX N, const float (&f)[Q],
                                           float* __restrict__ u,
                                           float* __restrict__ a,
                                           const Consts& k) {
-  const float lap = __fmul_rn(6.0f, fmaf(-(1.0f - wq(REST)), phi0, ssum));
+  NodeOut<float> o;
   float ax, ay, az;
-  compressive(phi0, gx, gy, gz, ax, ay, az);
-  a[n] = ax;
-  a[N + n] = ay;
-  a[2 * N + n] = az;
-
-  NodeOut o;
-  collide(f, phi0, gx, gy, gz, lap, k, o);
-#pragma unroll
-  for (int q = 0; q < Q; ++q) fout[q * N + n] = Store::encode_w(o.P[q], q);
-  u[n] = o.ux;
-  u[N + n] = o.uy;
-  u[2 * N + n] = o.uz;
+  node_eval(f, phi0, gx, gy, gz, ssum, k, o, ax, ay, az);
+  node_store<Store, IDX>(n, N, o, ax, ay, az, fout, u, a);
 }
 
+// Pull and phi stencil of the fluid node (x, y, z) of one grid, read from
+// global memory (halfway bounce-back on links from solid nodes), then the
+// node's evaluation. Returns false for a solid node (nothing evaluated).
 // IDX is int when 27 N fits in 31 bits (every offset then needs one 32-bit
 // multiply-add and one widening address computation), int64_t otherwise.
-// The node (x, y, z) of one grid: pull, stencil, collision, stores.
 template <typename Store, typename IDX>
-__device__ __forceinline__ void lb_node(int x, int y, int z,
-                                        const typename Store::T* __restrict__ fin,
-                                        typename Store::T* __restrict__ fout,
-                                        const float* __restrict__ phi,
-                                        float* __restrict__ u,
-                                        float* __restrict__ a,
-                                        const uint8_t* __restrict__ flags,
-                                        const Grid& g, const Consts& k) {
+__device__ __forceinline__ bool lb_node_eval(int x, int y, int z,
+                                             const typename Store::T* __restrict__ fin,
+                                             const float* __restrict__ phi,
+                                             const uint8_t* __restrict__ flags,
+                                             const Grid& g, const Consts& k,
+                                             NodeOut<float>& o, float& ax,
+                                             float& ay, float& az) {
   const IDX nx = g.nx;
   const IDX nxy = (IDX)g.nx * g.ny;
   const IDX N = (IDX)g.N;
   const IDX n = x + nx * y + nxy * z;
   const uint8_t fl = flags[n];
-  if (fl & FLAG_SOLID) return;
+  if (fl & FLAG_SOLID) return false;
   const IDX xo[3] = {(IDX)wrap(x, -1, g.nx), (IDX)x, (IDX)wrap(x, 1, g.nx)};
   const IDX yo[3] = {wrap(y, -1, g.ny) * nx, y * nx, wrap(y, 1, g.ny) * nx};
   const IDX zo[3] = {wrap(z, -1, g.nz) * nxy, z * nxy, wrap(z, 1, g.nz) * nxy};
@@ -296,7 +329,123 @@ __device__ __forceinline__ void lb_node(int x, int y, int z,
     const float vm = __ldg(phi + (xo[1 - cx(q)] + yz[1 - cy(q)][1 - cz(q)]));
     stencil_pair(q, vp, vm, gx, gy, gz, ssum);
   }
-  lb_finish<Store, IDX>(n, N, f, phi0, gx, gy, gz, ssum, fout, u, a, k);
+  node_eval(f, phi0, gx, gy, gz, ssum, k, o, ax, ay, az);
+  return true;
+}
+
+// The node (x, y, z) of one grid: pull, stencil, collision, stores.
+template <typename Store, typename IDX>
+__device__ __forceinline__ void lb_node(int x, int y, int z,
+                                        const typename Store::T* __restrict__ fin,
+                                        typename Store::T* __restrict__ fout,
+                                        const float* __restrict__ phi,
+                                        float* __restrict__ u,
+                                        float* __restrict__ a,
+                                        const uint8_t* __restrict__ flags,
+                                        const Grid& g, const Consts& k) {
+  NodeOut<float> o;
+  float ax, ay, az;
+  if (!lb_node_eval<Store, IDX>(x, y, z, fin, phi, flags, g, k, o, ax, ay, az))
+    return;
+  const IDX n = x + (IDX)g.nx * y + (IDX)g.nx * g.ny * z;
+  node_store<Store, IDX>(n, (IDX)g.N, o, ax, ay, az, fout, u, a);
+}
+
+// Evaluation of an x pair of fluid nodes (x0, x0 + 1) away from walls from
+// its 27 pulled population pairs and the 9 phi rows of its stencil, each
+// row given as (phi(x0 - 1), (phi(x0), phi(x0 + 1)), phi(x0 + 2)); rows
+// indexed [dy + 1][dz + 1]. Packed pair arithmetic, bit-identical to
+// node_eval on each node.
+__device__ __forceinline__ void pair_eval(const float2 (&f)[Q],
+                                          const float2 (&pc)[3][3],
+                                          const float (&pl)[3][3],
+                                          const float (&pr)[3][3],
+                                          const Consts& k, NodeOut<float2>& o,
+                                          float2& ax, float2& ay, float2& az) {
+  // phi at x + d for both nodes of the pair, d = -1, 0, +1
+  auto shifted = [&](int b, int c, int d) {
+    return d == 0 ? pc[b][c]
+         : d > 0 ? make_float2(pc[b][c].y, pr[b][c])
+                 : make_float2(pl[b][c], pc[b][c].x);
+  };
+  const float2 phi0 = pc[1][1];
+  float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx, ssum = gx;
+#pragma unroll
+  for (int q = 0; q < REST; ++q) {
+    const float2 vp = shifted(1 + cy(q), 1 + cz(q), cx(q));
+    const float2 vm = shifted(1 - cy(q), 1 - cz(q), -cx(q));
+    stencil_pair(q, vp, vm, gx, gy, gz, ssum);
+  }
+  node_eval(f, phi0, gx, gy, gz, ssum, k, o, ax, ay, az);
+}
+
+// An x pair of nodes (x0, x0 + 1), x0 even, both fluid and away from walls:
+// pull, stencil, collision and stores with two nodes per thread, the
+// arithmetic in packed pair operations. Loads and stores of the pair are
+// one aligned access per population, phi row and field; the pulled
+// populations of the links with c_x = +1 (-1) take the element left of
+// (right of) the pair from a second load, with the periodic wrap in x.
+// Bit-identical to lb_node on each node.
+template <typename Store>
+__device__ __forceinline__ void lb_pair(int x0, int y, int z,
+                                        const typename Store::T* __restrict__ fin,
+                                        typename Store::T* __restrict__ fout,
+                                        const float* __restrict__ phi,
+                                        float* __restrict__ u,
+                                        float* __restrict__ a, const Grid& g,
+                                        const Consts& k) {
+  using T = typename Store::T;
+  using T2 = typename Store::T2;
+  const int nx = g.nx;
+  const int nxy = g.nx * g.ny;
+  const int N = (int)g.N;
+  const int n = x0 + nx * y + nxy * z;
+  // the element left of the pair and the one right of it (x wraps)
+  const int xl = (x0 == 0) ? nx - 1 : x0 - 1;
+  const int xr = (x0 + 2 == nx) ? 0 : x0 + 2;
+  const int yo[3] = {wrap(y, -1, g.ny) * nx, y * nx, wrap(y, 1, g.ny) * nx};
+  const int zo[3] = {wrap(z, -1, g.nz) * nxy, z * nxy, wrap(z, 1, g.nz) * nxy};
+
+  float2 pc[3][3];
+  float pl[3][3], pr[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int row = yo[b] + zo[c];
+      pc[b][c] = __ldg(reinterpret_cast<const float2*>(phi + row + x0));
+      pl[b][c] = __ldg(phi + row + xl);
+      pr[b][c] = __ldg(phi + row + xr);
+    }
+
+  // pulled populations f*_q(x - c_q) of both nodes
+  float2 f[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const T* src = fin + q * N + yo[1 - cy(q)] + zo[1 - cz(q)];
+    const T2 own = __ldg(reinterpret_cast<const T2*>(src + x0));
+    T2 v;
+    if (cx(q) == 0)
+      v = own;
+    else if (cx(q) > 0)
+      v = Store::pack(__ldg(src + xl), Store::lo(own));
+    else
+      v = Store::pack(Store::hi(own), __ldg(src + xr));
+    f[q] = Store::decode2(v, q);
+  }
+
+  NodeOut<float2> o;
+  float2 ax, ay, az;
+  pair_eval(f, pc, pl, pr, k, o, ax, ay, az);
+  *reinterpret_cast<float2*>(a + n) = ax;
+  *reinterpret_cast<float2*>(a + N + n) = ay;
+  *reinterpret_cast<float2*>(a + 2 * N + n) = az;
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    *reinterpret_cast<T2*>(fout + q * N + n) = Store::encode_w2(o.P[q], q);
+  *reinterpret_cast<float2*>(u + n) = o.ux;
+  *reinterpret_cast<float2*>(u + N + n) = o.uy;
+  *reinterpret_cast<float2*>(u + 2 * N + n) = o.uz;
 }
 
 // mbarrier and bulk-copy primitives (PTX): a CTA-local barrier that counts
@@ -558,6 +707,263 @@ lb_collide(const typename Store::T* __restrict__ fin,
   lb_node<Store, IDX>(x, y, z, fin, fout, phi, u, a, flags, g, k);
 }
 
+// Two nodes per thread: block (LB2_PX, LB2_PY) covers 2 LB2_PX nodes of
+// LB2_PY rows of one plane. A pair with a solid node or a wall neighbour
+// (bounce-back links) runs the one-node path for each of its nodes.
+template <typename Store>
+__global__ void __launch_bounds__(LB2_PX * LB2_PY)
+lb_collide_pair(const typename Store::T* __restrict__ fin,
+                typename Store::T* __restrict__ fout, const float* __restrict__ phi,
+                float* __restrict__ u, float* __restrict__ a,
+                const uint8_t* __restrict__ flags, Grid g, Consts k) {
+  const int x0 = 2 * (blockIdx.x * LB2_PX + threadIdx.x);
+  const int y = blockIdx.y * LB2_PY + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x0 >= g.nx || y >= g.ny) return;
+  const int n = x0 + g.nx * (y + g.ny * z);
+  const uchar2 fl = *reinterpret_cast<const uchar2*>(flags + n);
+  if (((fl.x | fl.y) & (FLAG_SOLID | FLAG_NEAR)) == 0) {
+    lb_pair<Store>(x0, y, z, fin, fout, phi, u, a, g, k);
+  } else {
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j)
+      lb_node<Store, int>(x0 + j, y, z, fin, fout, phi, u, a, flags, g, k);
+  }
+}
+
+// TMA-tiled collide-stream (CACL_OPT_LB_PIPE = 3). A tile is TX consecutive
+// nodes of one row (x0 .. x0 + TX - 1, row y, plane z), two nodes per
+// thread, one tile per block. The tensor memory accelerator copies into
+// shared memory, completing on an mbarrier: for each of the 9 (c_y, c_z)
+// lines the three population rows q = 3 l .. 3 l + 2 of source row
+// (y - c_y, z - c_z), columns x0 - PAD .. x0 + TX + PAD - 1 (PAD = 16 bytes
+// of elements, so that every copy starts on a 16-byte boundary), and the 9
+// phi rows (y + dy, z + dz), columns x0 - 4 .. x0 + TX + 3; the 18 copies
+// are issued by 18 lanes of the first warp. y and z wrap through the copy
+// coordinates; the elements left of x = 0 and right of x = nx - 1 come back
+// as the fill value and the block patches the two it needs from global
+// memory. Every thread reads its pair's operands at fixed offsets from one
+// shared address (no per-element address arithmetic), evaluates the pair
+// (pair_eval) and writes f*, u and a into an output tile, which one thread
+// stores with three tensor copies. Pairs with a solid node or a wall
+// neighbour read global memory (lb_node_eval); solid nodes get f* = 0,
+// u = 0, a = 0. Bit-identical to lb_node at fluid nodes.
+template <typename Store, int TX>
+struct TmaTile {
+  using T = typename Store::T;
+  static constexpr int ES = (int)sizeof(T);
+  static constexpr int PAD = 16 / ES;
+  static constexpr int W = TX + 2 * PAD;                         // row, elements
+  static constexpr int LINE_B = (3 * W * ES + 127) / 128 * 128;  // 3 rows of a line
+  static constexpr int PADP = 4;
+  static constexpr int WP = TX + 2 * PADP;
+  static constexpr int ROWP_B = (WP * 4 + 127) / 128 * 128;
+  static constexpr int IN_B = 9 * LINE_B + 9 * ROWP_B;
+  static constexpr int OUTF_B = Q * TX * ES;                     // f* of the tile
+  static constexpr int OUTV_B = 3 * TX * 4;                      // u or a
+  static constexpr int SMEM_B = IN_B + OUTF_B + 2 * OUTV_B + 64;
+  static constexpr uint32_t TX_BYTES = 27u * W * ES + 9u * WP * 4;
+  static_assert(W <= 256 && WP <= 256, "tensor copy boxes hold at most 256 elements");
+  static_assert(OUTF_B % 128 == 0 && OUTV_B % 128 == 0, "output boxes 128-byte aligned");
+};
+
+struct LbTmaArgs {
+  CUtensorMap fin;   // (x, y, z, q), box (W, 1, 1, 3)
+  CUtensorMap fout;  // (x, y, z, q), box (TX, 1, 1, 27)
+  CUtensorMap phi;   // (x, y, z), box (WP, 1, 1)
+  CUtensorMap u;     // (x, y, z, component), box (TX, 1, 1, 3)
+  CUtensorMap a;
+};
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0,
+                                            int c1, int c2, int c3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0,
+                                            int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, int c0, int c1,
+                                             int c2, int c3, const void* src) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group"
+      " [%0, {%1, %2, %3, %4}], [%5];\n" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+// the stores committed so far have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+// orders this thread's shared-memory accesses with later tensor copies
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+template <typename Store, int TX>
+__global__ void __launch_bounds__(TX / 2)
+lb_collide_tma(const __grid_constant__ LbTmaArgs m,
+               const typename Store::T* __restrict__ fin,
+               const float* __restrict__ phi, const uint8_t* __restrict__ flags,
+               Grid g, Consts k, unsigned* __restrict__ wait_err) {
+  using L = TmaTile<Store, TX>;
+  using T = typename Store::T;
+  using T2 = typename Store::T2;
+  extern __shared__ __align__(128) unsigned char lbt_smem[];
+  unsigned char* const base = lbt_smem;
+  T* const sf = reinterpret_cast<T*>(lbt_smem + L::IN_B);
+  float* const su = reinterpret_cast<float*>(lbt_smem + L::IN_B + L::OUTF_B);
+  float* const sa = su + 3 * TX;
+  uint64_t* const bar = reinterpret_cast<uint64_t*>(lbt_smem + L::IN_B + L::OUTF_B +
+                                                    2 * L::OUTV_B);
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * TX, y = blockIdx.y, z = blockIdx.z;
+
+  if (tid < 32) {
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      mbar_arrive_expect_tx(bar, L::TX_BYTES);
+    }
+    __syncwarp();
+    if (tid < 9) {
+      tma_load_4d(base + tid * L::LINE_B, &m.fin, x0 - L::PAD,
+                  wrap(y, -(tid % 3 - 1), g.ny), wrap(z, -(tid / 3 - 1), g.nz), 3 * tid,
+                  bar);
+    } else if (tid < 18) {
+      const int j = tid - 9;
+      tma_load_3d(base + 9 * L::LINE_B + j * L::ROWP_B, &m.phi, x0 - L::PADP,
+                  wrap(y, j % 3 - 1, g.ny), wrap(z, j / 3 - 1, g.nz), bar);
+    }
+  }
+  __syncthreads();  // the barrier is initialised before anyone waits on it
+  const bool ok = mbar_wait(bar, 0);
+  if (__syncthreads_or(!ok)) {
+    // give up: record it, let the copies in flight land (bounded), return
+    if (tid == 0) {
+      atomicOr(wait_err, 1u);
+      mbar_wait(bar, 0);
+    }
+    return;
+  }
+  const int nx = g.nx, nxy = g.nx * g.ny, N = (int)g.N;
+
+  // periodic wrap in x: the element left of x = 0 and the one right of
+  // x = nx - 1, for the 27 population rows and the 9 phi rows
+  const bool left = (x0 == 0), right = (x0 + TX >= nx);
+  if (left || right) {
+#pragma unroll 1
+    for (int e = tid; e < 72; e += TX / 2) {
+      const int side = e / 36, r = e - 36 * side;
+      if (side == 0 ? !left : !right) continue;
+      const int xs = (side == 0) ? nx - 1 : 0;
+      if (r < Q) {
+        const int col = (side == 0) ? L::PAD - 1 : L::PAD + (nx - x0);
+        const int src = wrap(z, -cz(r), g.nz) * nxy + wrap(y, -cy(r), g.ny) * nx + xs;
+        T* dst = reinterpret_cast<T*>(base + (r / 3) * L::LINE_B) + (r % 3) * L::W + col;
+        *dst = fin[r * N + src];
+      } else {
+        const int j = r - Q;
+        const int col = (side == 0) ? L::PADP - 1 : L::PADP + (nx - x0);
+        const int src = wrap(z, j / 3 - 1, g.nz) * nxy + wrap(y, j % 3 - 1, g.ny) * nx + xs;
+        float* dst = reinterpret_cast<float*>(base + 9 * L::LINE_B + j * L::ROWP_B) + col;
+        *dst = phi[src];
+      }
+    }
+    __syncthreads();
+  }
+
+  const int x = x0 + 2 * tid;
+  if (x < nx) {
+    const int n = x + nx * y + nxy * z;
+    const uchar2 fl = *reinterpret_cast<const uchar2*>(flags + n);
+    if (((fl.x | fl.y) & (FLAG_SOLID | FLAG_NEAR)) == 0) {
+      float2 f[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const T* ln = reinterpret_cast<const T*>(base + (q / 3) * L::LINE_B) +
+                      (q % 3) * L::W + L::PAD + 2 * tid;
+        const T2 own = *reinterpret_cast<const T2*>(ln);
+        T2 v;
+        if (cx(q) == 0)
+          v = own;
+        else if (cx(q) > 0)
+          v = Store::pack(ln[-1], Store::lo(own));
+        else
+          v = Store::pack(Store::hi(own), ln[2]);
+        f[q] = Store::decode2(v, q);
+      }
+      float2 pc[3][3];
+      float pl[3][3], pr[3][3];
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float* r = reinterpret_cast<const float*>(
+                               base + 9 * L::LINE_B + (3 * c + b) * L::ROWP_B) +
+                           L::PADP + 2 * tid;
+          pc[b][c] = *reinterpret_cast<const float2*>(r);
+          pl[b][c] = r[-1];
+          pr[b][c] = r[2];
+        }
+      NodeOut<float2> o;
+      float2 ax, ay, az;
+      pair_eval(f, pc, pl, pr, k, o, ax, ay, az);
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        *reinterpret_cast<T2*>(sf + q * TX + 2 * tid) = Store::encode_w2(o.P[q], q);
+      *reinterpret_cast<float2*>(su + 2 * tid) = o.ux;
+      *reinterpret_cast<float2*>(su + TX + 2 * tid) = o.uy;
+      *reinterpret_cast<float2*>(su + 2 * TX + 2 * tid) = o.uz;
+      *reinterpret_cast<float2*>(sa + 2 * tid) = ax;
+      *reinterpret_cast<float2*>(sa + TX + 2 * tid) = ay;
+      *reinterpret_cast<float2*>(sa + 2 * TX + 2 * tid) = az;
+    } else {
+#pragma unroll 1
+      for (int j = 0; j < 2; ++j) {
+        NodeOut<float> on;
+        float bx = 0.f, by = 0.f, bz = 0.f;
+        const int c = 2 * tid + j;
+        if (lb_node_eval<Store, int>(x + j, y, z, fin, phi, flags, g, k, on, bx, by, bz)) {
+#pragma unroll
+          for (int q = 0; q < Q; ++q) sf[q * TX + c] = Store::encode_w(on.P[q], q);
+          su[c] = on.ux;
+          su[TX + c] = on.uy;
+          su[2 * TX + c] = on.uz;
+        } else {
+#pragma unroll
+          for (int q = 0; q < Q; ++q) sf[q * TX + c] = Store::encode_w(0.0f, q);
+          su[c] = su[TX + c] = su[2 * TX + c] = 0.f;
+        }
+        sa[c] = bx;
+        sa[TX + c] = by;
+        sa[2 * TX + c] = bz;
+      }
+    }
+  }
+  fence_proxy_async();
+  __syncthreads();
+  if (tid == 0) {
+    tma_store_4d(&m.fout, x0, y, z, 0, sf);
+    tma_store_4d(&m.u, x0, y, z, 0, su);
+    tma_store_4d(&m.a, x0, y, z, 0, sa);
+    bulk_commit();
+    bulk_wait_read();  // shared memory stays valid until the stores read it
+  }
+}
+
 // Batched collide-stream: virtual block b of the work-list is row block
 // (bx, y, z) of its case; rows of BX threads along x. Blocks stride through
 // the work-list (b, b + gridDim.x, ...) so that the rows in flight at any
@@ -614,6 +1020,67 @@ cudaError_t staged_setup(const Grid& g, int* grid) {
   return e;
 }
 
+constexpr int LBT_TX = 128;  // nodes per tile of the TMA-tiled collide-stream
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Row-major tensor map over (x, y, z[, k]) with element size es and the
+// given box; false if the driver rejects it.
+bool encode_map(CUtensorMap* m, int es, int rank, void* addr, const Grid& g,
+                int kdim, const cuuint32_t* box) {
+  auto fn = tensor_map_encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz,
+                              (cuuint64_t)kdim};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.nx * es, (cuuint64_t)g.nx * g.ny * es,
+                                 (cuuint64_t)g.N * es};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUtensorMapDataType dt =
+      es == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return fn(m, dt, (cuuint32_t)rank, addr, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename Store>
+cudaError_t tma_setup(cacl_ctx* c) {
+  using L = TmaTile<Store, LBT_TX>;
+  const Grid& g = c->g;
+  c->lbt_ok = false;
+  if (g.nx % 8 != 0 || (int64_t)Q * g.N >= (int64_t)INT32_MAX) return cudaSuccess;
+  const cuuint32_t boxf[4] = {(cuuint32_t)L::W, 1, 1, 3};
+  const cuuint32_t boxo[4] = {(cuuint32_t)LBT_TX, 1, 1, (cuuint32_t)Q};
+  const cuuint32_t boxp[3] = {(cuuint32_t)L::WP, 1, 1};
+  const cuuint32_t boxv[4] = {(cuuint32_t)LBT_TX, 1, 1, 3};
+  bool ok = true;
+  for (int i = 0; i < 2; ++i) {
+    ok = ok && encode_map(&c->lbt_fload[i], L::ES, 4, c->f[i], g, Q, boxf);
+    ok = ok && encode_map(&c->lbt_fstore[i], L::ES, 4, c->f[i], g, Q, boxo);
+    ok = ok && encode_map(&c->lbt_phi[i], 4, 3, c->phi[i], g, 1, boxp);
+  }
+  ok = ok && encode_map(&c->lbt_u, 4, 4, c->u, g, 3, boxv);
+  ok = ok && encode_map(&c->lbt_a, 4, 4, c->a, g, 3, boxv);
+  if (!ok) return cudaSuccess;  // the other collide-stream kernels remain
+  void* fn = (void*)lb_collide_tma<Store, LBT_TX>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       L::SMEM_B);
+  if (e != cudaSuccess) return e;
+  c->lbt_ok = true;
+  return cudaSuccess;
+}
+
 template <typename Store>
 void launch_store(cacl_ctx* c, const void* fin, void* fout, const float* phi) {
   using T = typename Store::T;
@@ -635,6 +1102,27 @@ void launch_store(cacl_ctx* c, const void* fin, void* fout, const float* phi) {
     void* args[] = {(void*)&fi, (void*)&fo, (void*)&phi, (void*)&u, (void*)&a,
                     (void*)&fl, (void*)&gg, (void*)&k, (void*)&ns, (void*)&err};
     cudaLaunchKernel(fn, dim3(grid), dim3(SEG), args, smem, c->stream);
+    return;
+  }
+  if (lb_tma_ok(c, fin, fout, phi)) {
+    const int fi = (fin == c->f[0]) ? 0 : 1;
+    LbTmaArgs m;
+    m.fin = c->lbt_fload[fi];
+    m.fout = c->lbt_fstore[1 - fi];
+    m.phi = c->lbt_phi[(phi == c->phi[0]) ? 0 : 1];
+    m.u = c->lbt_u;
+    m.a = c->lbt_a;
+    const dim3 grid((g.nx + LBT_TX - 1) / LBT_TX, g.ny, g.nz);
+    lb_collide_tma<Store, LBT_TX><<<grid, LBT_TX / 2, TmaTile<Store, LBT_TX>::SMEM_B,
+                                   c->stream>>>(m, (const T*)fin, phi, c->flags, g,
+                                                c->k, c->ticket + 1);
+    return;
+  }
+  if (lb_pair_ok(c, fin, fout, phi)) {
+    dim3 block(LB2_PX, LB2_PY, 1);
+    dim3 grid((g.nx / 2 + LB2_PX - 1) / LB2_PX, (g.ny + LB2_PY - 1) / LB2_PY, g.nz);
+    lb_collide_pair<Store><<<grid, block, 0, c->stream>>>(
+        (const T*)fin, (T*)fout, phi, c->u, c->a, c->flags, g, c->k);
     return;
   }
   dim3 block(LB_BX, LB_BY, 1);
@@ -659,6 +1147,27 @@ cudaError_t lb_init(cacl_ctx* c) {
   }
 }
 
+// Tensor maps of the TMA-tiled collide-stream over the context's own
+// buffers (set once the buffers exist, outside any graph capture).
+cudaError_t lb_tma_init(cacl_ctx* c) {
+  switch (c->p.storage) {
+    case CACL_F16_SHIFTED: return tma_setup<StoreF16>(c);
+    case CACL_BF16_SHIFTED: return tma_setup<StoreBF16>(c);
+    default: return tma_setup<StoreF32>(c);
+  }
+}
+
+// The TMA-tiled collide-stream (CACL_OPT_LB_PIPE = 3) runs on the
+// context's own population, phi, u and a buffers when nx is a multiple of 8
+// and 27 N < 2^31; otherwise the two-node kernel runs.
+bool lb_tma_ok(const cacl_ctx* c, const void* fin, const void* fout,
+               const void* phi) {
+  const bool fpair = (fin == c->f[0] && fout == c->f[1]) ||
+                     (fin == c->f[1] && fout == c->f[0]);
+  return c->lb_pipe == 3 && c->lbt_ok && fpair &&
+         (phi == c->phi[0] || phi == c->phi[1]);
+}
+
 // The copy-staged collide-stream (chosen by CACL_OPT_LB_PIPE = 1) needs
 // 16-byte aligned runs: nx a multiple of 16 bytes' worth of populations and
 // of 4, aligned fields; otherwise the direct kernel runs.
@@ -668,6 +1177,19 @@ bool lb_staged_ok(const cacl_ctx* c, const void* fin, const void* fout,
   auto al = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
   return c->lb_pipe == 1 && c->g.nx % pf == 0 && c->g.nx % 4 == 0 &&
          al(fin) && al(fout) && al(phi);
+}
+
+// The two-node collide-stream (the default, CACL_OPT_LB_PIPE = 0, and the
+// fallback of 3) needs nx even, 27 N below 2^31 (32-bit offsets) and buffers
+// aligned for the pair accesses; otherwise, or with CACL_OPT_LB_PIPE = 2,
+// one node per thread.
+bool lb_pair_ok(const cacl_ctx* c, const void* fin, const void* fout,
+                const void* phi) {
+  const uintptr_t fa = 2 * storage_bytes(c->p.storage) - 1;
+  auto al = [](const void* p, uintptr_t m) { return ((uintptr_t)p & m) == 0; };
+  return (c->lb_pipe == 0 || c->lb_pipe == 3) && c->g.nx % 2 == 0 &&
+         (int64_t)Q * c->g.N < (int64_t)INT32_MAX && al(fin, fa) && al(fout, fa) &&
+         al(phi, 7) && al(c->u, 7) && al(c->a, 7);
 }
 
 cudaError_t launch_lb(cacl_ctx* c, const void* fin, void* fout,

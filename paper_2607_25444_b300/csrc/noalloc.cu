@@ -15,6 +15,11 @@
 // fluid nodes, W = sum of chi(phi) with chi = phi (1 - phi) inside
 // (eps, 1 - eps), lambda = (M_ref - M*)/W (0 when W = 0), and
 // phi += lambda chi(phi) at fluid nodes. Sums are FP64, in a fixed order.
+// The update is rounded without bias, as in the context's correction: a
+// correction below the FP32 resolution of phi is applied on average instead
+// of being rounded away at every call. The rounding key is a call counter
+// the library keeps in the scratch array (it starts at zero when the
+// library is loaded and advances by one per call on that device).
 #include <mutex>
 
 #include "cacl_internal.cuh"
@@ -29,7 +34,8 @@ constexpr int64_t NA_MAX_NODES = (int64_t)NA_MAX_BLOCKS * NA_NODES_PER_BLOCK;
 constexpr int NA_FIN_THREADS = 1024;
 
 // [0, MAX): block sums of phi; [MAX, 2 MAX): block sums of chi;
-// [2 MAX, 2 MAX + 3): M*, W, lambda of the last call.
+// [2 MAX, 2 MAX + 3): M*, W, lambda of the last call; [2 MAX + 3]: the
+// call counter (the rounding key of the unbiased update), as 64-bit bits.
 static __device__ __align__(256) double g_noalloc_scratch[2 * NA_MAX_BLOCKS + 8];
 
 std::mutex g_setup_mu;
@@ -111,6 +117,8 @@ noalloc_finalize(double* __restrict__ scratch, int nb, double m_ref,
     scratch[2 * NA_MAX_BLOCKS + 0] = sm[0];
     scratch[2 * NA_MAX_BLOCKS + 1] = sw[0];
     scratch[2 * NA_MAX_BLOCKS + 2] = lam;
+    uint64_t* calls = reinterpret_cast<uint64_t*>(scratch + 2 * NA_MAX_BLOCKS + 3);
+    *calls += 1;
     if (out) {
       out[0] = sm[0];
       out[1] = sw[0];
@@ -123,10 +131,12 @@ __global__ void __launch_bounds__(NA_THREADS)
 noalloc_apply(float* __restrict__ phi, const uint8_t* __restrict__ solid,
               int64_t n, float eps, const double* __restrict__ scratch) {
   const float lam = (float)scratch[2 * NA_MAX_BLOCKS + 2];
+  const uint32_t key = (uint32_t)*reinterpret_cast<const uint64_t*>(
+      scratch + 2 * NA_MAX_BLOCKS + 3);
   const int64_t i = (int64_t)blockIdx.x * NA_THREADS + threadIdx.x;
   if (i >= n || solid[i]) return;
   const float v = phi[i];
-  phi[i] = fmaf(lam, band_weight(v, eps), v);
+  phi[i] = cacl::add_unbiased(v, lam * band_weight(v, eps), key, (uint64_t)i);
 }
 
 }  // namespace
@@ -139,8 +149,27 @@ extern "C" cacl_status cacl_volume_correct_noalloc(float* phi,
   if (!phi || !solid || n < 1) return CACL_ERR_ARG;
   if (!(eps_phi > 0.0 && eps_phi < 0.5)) return CACL_ERR_ARG;
   if (n > NA_MAX_NODES) return CACL_ERR_TOO_LARGE;
+  // phi, solid and out must live on the current device: the scratch array
+  // used below is that device's copy
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CACL_ERR_CUDA;
+  const void* ptrs[3] = {phi, solid, out};
+  for (const void* q : ptrs) {
+    if (!q) continue;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+      cudaGetLastError();  // clear the error this query recorded
+      return CACL_ERR_ARG;
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+      return CACL_ERR_ARG;
+    if (at.device != dev) return CACL_ERR_ARG;
+  }
   double* scratch = nullptr;
   if (scratch_on_current_device(&scratch) != cudaSuccess) return CACL_ERR_CUDA;
+  // clear a non-sticky error left by earlier unrelated work, so that the
+  // check after the launches reports these launches only
+  cudaGetLastError();
   cudaStream_t st = (cudaStream_t)stream;
   const int nb = (int)((n + NA_NODES_PER_BLOCK - 1) / NA_NODES_PER_BLOCK);
   const float eps = (float)eps_phi;

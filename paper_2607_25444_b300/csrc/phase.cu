@@ -1,7 +1,7 @@
 // phase.cu -- conservative Allen-Cahn update of phi at fluid nodes
-// (Sect. 2.2: Eqs. phi_update_muscl, divF, face_flux_def, slope_minmod_x,
+// (Sect. 2.1.1: Eqs. phi_update_muscl, divF, face_flux_def, slope_minmod_x,
 // minmod, recon_lr_x, upwind_select_x, source_sharp; Eq. lap_iso), plus the
-// per-block partial sums of the volume correction (Sect. 2.4,
+// per-block partial sums of the volume correction (Sect. 2.3,
 // Eqs. tentative_phase_field_mass, mass_correction_normalization).
 //
 // Each block owns a TX x TY column of nodes and marches up a chunk of ZC

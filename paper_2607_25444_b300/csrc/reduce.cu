@@ -1,4 +1,4 @@
-// reduce.cu -- volume correction (Sect. 2.4, Eqs. mass_defect,
+// reduce.cu -- volume correction (Sect. 2.3, Eqs. mass_defect,
 // interface_weight_mass_correction, mass_correction_normalization,
 // mass_corrected_phi), the initial state (Eq. feq3 at p* = 0), the mass
 // reference (Eq. phase_field_mass) and small state queries.

@@ -386,6 +386,71 @@ def test_lb_staged_pipeline(storage, shape):
         assert np.array_equal(a, b)
 
 
+def _lb_pipes_agree(p, solid, phi, u, pipes, steps=20):
+    from paper_2607_25444_b300 import cacl
+    runs = []
+    for pipe in pipes:
+        g = _solver(p)
+        g.set_option(cacl.OPT_LB_PIPE, pipe)
+        g.set_geometry(solid)
+        g.set_fields(phi, u)
+        g.step(steps)
+        g.check_finite()
+        ph, uu, ps = g.fields()
+        runs.append((ph, uu, ps, g.populations()))
+    for other in runs[1:]:
+        for a, b in zip(runs[0], other):
+            assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("shape", [(64, 10, 9), (130, 6, 8), (2, 5, 6), (36, 12, 10),
+                                   (136, 6, 8), (16, 12, 10), (256, 4, 5)])
+def test_lb_kernels_bit_identical(storage, shape):
+    """Two nodes per thread with packed pair arithmetic (the default), one
+    node per thread, and the TMA-tiled form (where nx is a multiple of 8)
+    give bit for bit the same populations, u, p* and phi over 20 full steps: one tile row narrower than a tile (nx = 64, 16), two tiles with
+    both x edges (256), a partial last tile (136), a partial last block with
+    the x wrap inside it for the pair kernel (nx = 130), a row that is a
+    single pair (both neighbours wrap onto the row itself) and a small box."""
+    nx, ny, nz = shape
+    p, solid, phi = _droplet_case(nx=nx, ny=ny, nz=nz, theta=70.0)
+    p = dict(p, storage=storage, rho_g=0.3, nu_g=0.08)
+    u = I.fast_uniform((3, nz, ny, nx), seed=5, lo=-0.02, hi=0.02).astype(np.float32)
+    u[:, solid == 1] = 0.0
+    _lb_pipes_agree(p, solid, phi, u, (0, 2, 3))
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("kind", ["orifice", "rough", "periodic"])
+def test_lb_kernels_mixed_pairs(storage, kind):
+    """Pairs next to walls (bounce-back links) take the one-node path inside
+    the same tiles and warps as interior pairs: orifice plate and rough
+    floor; and a fully periodic box (every row wraps in y and z), all bit
+    for bit equal to one node per thread."""
+    if kind == "orifice":
+        nx, ny, nz = 24, 24, 40
+        solid = I.orifice_plate(nx, ny, nz, 16, 4, 8)
+        c = (12.0, 12.0, 30.0)
+        per = (1, 1, 0)
+    elif kind == "rough":
+        nx, ny, nz = 24, 20, 14
+        solid = I.rough_wall_z(nx, ny, nz, 3, seed=5)
+        c = (12.0, 10.0, 4.0)
+        per = (1, 1, 0)
+    else:
+        nx, ny, nz = 32, 12, 10
+        solid = np.zeros((nz, ny, nx), np.uint8)
+        c = (16.0, 6.0, 5.0)
+        per = (1, 1, 1)
+    p = I.base_params(nx, ny, nz, sigma=0.01, rho_g=0.2, nu_g=0.1,
+                      theta_deg=60.0, gravity=(0.0, 0.0, -2e-5), periodic=per,
+                      storage=storage)
+    phi = I.droplet(nx, ny, nz, c, 6.0, p["width"])
+    phi[solid == 1] = 0.0
+    _lb_pipes_agree(p, solid, phi, None, (0, 2, 3))
+
+
 def _quantize(f, storage):
     """Round f_i / w_i to the 16-bit storage (nearest even) and scale back."""
     import torch

@@ -1,5 +1,5 @@
 """Pins of the oracle's wall-normal reconstruction, donor selection and ghost
-value (Sect. 2.3, Eqs. local_wall_normal .. contact_angle_localization)."""
+value (Sect. 2.2, Eqs. local_wall_normal .. contact_angle_localization)."""
 import math
 
 import numpy as np
@@ -216,7 +216,7 @@ def test_ghost_closed_forms_flat_wall():
 
 
 def test_ghost_cot_regularisation():
-    """|sin theta_c| below tolerance: cot replaced by +-1e6 (Sect. 2.3)."""
+    """|sin theta_c| below tolerance: cot replaced by +-1e6 (Sect. 2.2)."""
     nw = np.array([0.0, 0.0, -1.0])
     rfs = np.array([0.0, 0.0, -1.0])
     grad = np.array([0.1, 0.0, 0.0])

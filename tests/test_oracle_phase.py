@@ -1,5 +1,5 @@
-"""Pins of the oracle's phase-field update and volume correction (Sect. 2.2,
-Eq. phi_update_muscl and the MUSCL-minmod scheme; Sect. 2.4)."""
+"""Pins of the oracle's phase-field update and volume correction (Sect. 2.1.1,
+Eq. phi_update_muscl and the MUSCL-minmod scheme; Sect. 2.3)."""
 import os
 
 import numpy as np
@@ -99,7 +99,7 @@ def test_periodic_update_conserves_mass_by_telescoping():
 
 
 def test_volume_correction_restores_mass_in_band_only():
-    """Sect. 2.4: after the correction the fluid mass equals M_ref; nodes
+    """Sect. 2.3: after the correction the fluid mass equals M_ref; nodes
     outside (eps, 1 - eps) are untouched; solid nodes are untouched."""
     n = 12
     solid = I.walls_z(n, n, n)
