@@ -113,7 +113,7 @@ class ClockSampler:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index),
                  f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE,
+                 "-lms", "50"], stdout=subprocess.PIPE,
                 stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -255,6 +255,58 @@ def impact_sweep_cases(ncases=48, storage="f16"):
         u[2] = np.where(phi > 0.5, -d["u0"], 0.0)
         out.append((p, solid, phi, u))
         assert _m.isfinite(d["u0"])
+    return out
+
+
+def median_steps_time(solver, torch, stream, steps, repeats):
+    """Median over `repeats` of the CUDA-event time of `steps` steps."""
+    times = []
+    for _ in range(repeats):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return float(np.median(times))
+
+
+def paper_workloads(args, torch, cacl, stream):
+    """Throughput on the paper-shaped workloads other than the headline: the
+    spreading case of Sect. 3.2 (128^3, cap R = 24, theta = 60 deg, density
+    ratio 10, equal kinematic viscosities, sigma = 0.005) with FP32 and the
+    16-bit population storage, and the orifice passage of Sect. 3.4
+    (128 x 128 x 256, plate 8 thick at z = 128 with a square hole of side
+    24, drop R = 20 above it, density ratio 50, Bond number 1, theta =
+    60 deg) in FP32. Synthetic seeded inputs."""
+    from paper_2607_25444_b300 import inputs as I
+    out = {}
+    steps = max(20, min(args.steps, 100))
+    cases = [("spreading_128cube", I.spreading_128(60.0), ("f32", "f16", "bf16")),
+             ("orifice_128x128x256", I.orifice_128x128x256(24, 60.0, 1.0), ("f32",))]
+    for name, (p, solid, phi), storages in cases:
+        rec = {"grid": [p["nx"], p["ny"], p["nz"]],
+               "fluid_nodes": int((solid == 0).sum())}
+        N = phi.size
+        for st in storages:
+            sv = cacl.Solver(dict(p, storage=st))
+            sv.set_geometry(solid)
+            sv.set_fields(phi)
+            sv.step(5)
+            dtv = median_steps_time(sv, torch, stream, steps, 3)
+            sv.check_finite()
+            sv.close()
+            rec[st] = {"value": N * steps / dtv / 1e6, "unit": "MLUPS",
+                       "ms_per_step": dtv / steps * 1e3,
+                       "step_frac": N * step_bytes(st) * steps / dtv / 1e9
+                                    / measured_peaks()[0]}
+        if "f16" in rec:
+            rec["f16"]["speedup_vs_f32"] = rec["f16"]["value"] / rec["f32"]["value"]
+            rec["bf16"]["speedup_vs_f32"] = rec["bf16"]["value"] / rec["f32"]["value"]
+        rec["steps"] = steps
+        out[name] = rec
     return out
 
 
@@ -439,6 +491,158 @@ def run_curved_wall(args):
                       "results": out}), flush=True)
 
 
+def run_inference(args):
+    """Wettability inference shaped like the paper's footprint analysis
+    (contact angle from the droplet's wetted footprint): 96^3 between flat
+    walls, the bottom wall's contact angle in 8 x 8 patches of 12 x 12 nodes
+    drawn from U[45, 135] deg (seeded), the top wall at 90 deg, a drop of
+    radius 16 resting on the bottom wall, sigma = 0.01, nu = 0.1. The target
+    is the footprint phi(x, y, z = 1) after a rollout of --inf-steps steps
+    (2000) with the true angles; the angles are recovered from a uniform
+    90 deg start by Adam on the 64 patch angles with dL/dtheta from the
+    hand-written adjoint (checkpoints every --inf-every steps, FP32 forward,
+    FP64 accumulation of the gradients), L = sum over z = 1 of
+    (phi - phi_target)^2. Prints one JSON line."""
+    import torch
+
+    from paper_2607_25444_b300 import cacl
+    from paper_2607_25444_b300 import inputs as I
+    torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    stream = torch.cuda.current_stream()
+    n = 96
+    p = I.base_params(n, n, n, sigma=0.01, nu_l=0.1, nu_g=0.1, theta_deg=90.0)
+    solid = I.walls_z(n, n, n)
+    phi0 = I.droplet(n, n, n, (n / 2, n / 2, 0.5), 16.0, p["width"])
+    s = cacl.Solver(p)
+    s.set_geometry(solid)
+    idx = s.wall_list()["idx"]
+    x, y, z = idx % n, (idx // n) % n, idx // (n * n)
+    bottom = z == 0
+    patch = (y // 12) * 8 + (x // 12)
+    truth = I.SplitMix64(2025).array(64, 45.0, 135.0)
+    steps, every = args.inf_steps, args.inf_every
+
+    def angles(theta_patch):
+        th = np.full(idx.size, 90.0, np.float32)
+        th[bottom] = np.asarray(theta_patch, np.float64)[patch[bottom]]
+        return th
+
+    # target footprint
+    s.set_fields(phi0)
+    s.set_wall_angles(angles(truth))
+    s.step(steps)
+    target = s.fields()[0][1].copy()
+    # forward cost at this size (plain steps)
+    s.set_fields(phi0)
+    s.step(10)
+    torch.cuda.synchronize()
+    t_fwd = median_steps_time(s, torch, stream, 200, 3) / 200
+    tgt = torch.from_numpy(target).cuda()
+    theta = np.full(64, 90.0)
+    m = np.zeros(64)
+    v = np.zeros(64)
+    lr, b1, b2 = 3.0, 0.9, 0.999
+    hist = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    t_bwd = []
+    touched = None
+    for it in range(args.inf_iters):
+        s.set_fields(phi0)
+        s.set_wall_angles(angles(theta))
+        e0.record(stream)
+        s.adjoint_forward(steps, every)
+        e1.record(stream)
+        phi = torch.empty(n ** 3, dtype=torch.float32, device="cuda")
+        s.fields_device(phi=phi)
+        ph1 = phi.view(n, n, n)[1]
+        loss = float(((ph1 - tgt) ** 2).sum().item())
+        g = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
+        g.view(n, n, n)[1] = 2.0 * (ph1 - tgt)
+        dth = torch.zeros(idx.size, dtype=torch.float64, device="cuda")
+        dsg = torch.zeros(1, dtype=torch.float64, device="cuda")
+        s.adjoint_backward(g, dth, dsg)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        t_bwd.append(e1.elapsed_time(e2) / 1e3 / steps)
+        gw = dth.cpu().numpy()
+        gp = np.bincount(patch[bottom], weights=gw[bottom], minlength=64)
+        if touched is None:
+            touched = np.abs(gp) > 1e-6 * np.abs(gp).max()
+        hist.append(loss)
+        m = b1 * m + (1 - b1) * gp
+        v = b2 * v + (1 - b2) * gp * gp
+        mh = m / (1 - b1 ** (it + 1))
+        vh = v / (1 - b2 ** (it + 1))
+        theta = np.clip(theta - lr * mh / (np.sqrt(vh) + 1e-12), 20.0, 160.0)
+    free_b, total_b = torch.cuda.mem_get_info()
+    s.close()
+    err = np.abs(theta - truth)
+    line = {
+        "metric": "wettability inference from the footprint (adjoint)",
+        "workload": f"{n}^3 flat walls, bottom-wall theta in 8x8 patches "
+                    "U[45,135] deg (seeded), R=16, sigma=0.01, nu=0.1",
+        "steps": steps, "ckpt_every": every, "iterations": args.inf_iters,
+        "loss_first": hist[0], "loss_last": hist[-1],
+        "loss_reduction": hist[0] / max(hist[-1], 1e-300),
+        "patches_touched": int(touched.sum()),
+        "theta_err_touched_mean_deg": float(err[touched].mean()),
+        "theta_err_touched_max_deg": float(err[touched].max()),
+        "theta_err_start_touched_mean_deg": float(np.abs(90.0 - truth)[touched].mean()),
+        "theta_err_all_mean_deg": float(err.mean()),
+        "forward_ms_per_step": t_fwd * 1e3,
+        "backward_ms_per_step": float(np.median(t_bwd)) * 1e3,
+        "backward_over_forward": float(np.median(t_bwd)) / t_fwd,
+        "device_gb_in_use": (total_b - free_b) / 1e9,
+        "loss_history": [round(h, 6) for h in hist],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_c2_accuracy(args):
+    """Storage-mode error on the spreading workload at its configured size
+    (128^3, Sect. 3.2 shape, theta = 60 deg): FP32, FP16 and BF16 population
+    storage against the FP64 oracle after --c2-steps steps (the horizon the
+    oracle runs on this host's cores in a few minutes): the spreading radius
+    r = sqrt(A / pi) of the wetted area {phi > 1/2} on the first fluid layer,
+    and the largest phi difference. Prints one JSON line."""
+    import torch
+
+    from oracle import oracle as O
+    from paper_2607_25444_b300 import cacl
+    from paper_2607_25444_b300 import inputs as I
+    torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    p, solid, phi = I.spreading_128(60.0)
+    steps = args.c2_steps
+    o = O.Oracle(p)
+    o.set_geometry(solid)
+    o.set_fields(phi.astype(np.float64))
+    t0 = time.perf_counter()
+    o.step(steps)
+    t_cpu = time.perf_counter() - t0
+    ref = o.fields()[0]
+
+    def radius(f):
+        return float(np.sqrt((f[1] > 0.5).sum() / np.pi))
+
+    r_ref = radius(ref)
+    out = {"metric": "spreading radius error vs the FP64 oracle, 128^3",
+           "steps": steps, "oracle_seconds": t_cpu, "r_oracle": r_ref}
+    for st in ("f32", "f16", "bf16"):
+        sv = cacl.Solver(dict(p, storage=st))
+        sv.set_geometry(solid)
+        sv.set_fields(phi)
+        sv.step(steps)
+        f = sv.fields()[0]
+        sv.close()
+        out[st] = {"r": radius(f), "r_err": abs(radius(f) - r_ref),
+                   "phi_max_err": float(np.abs(f - ref).max())}
+    print(json.dumps(out), flush=True)
+
+
 def run_cuda(args):
     import torch
     rank, world, local = dist_env()
@@ -464,23 +668,27 @@ def run_cuda(args):
     # and the two ghost passes when there are walls
     kernels_per_step = 3 + (2 if W > 0 else 0)
 
-    # warm-up, then K timed steps bracketed by barrier + synchronize
+    # warm-up, then REPEATS x K timed steps, each bracketed by barrier +
+    # synchronize; the median repeat is the measurement
     s.step(args.warmup)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
+    times = []
     with ClockSampler(local) as clk:
-        ev0.record(stream)
-        s.step(args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    dt = ev0.elapsed_time(ev1) / 1e3
+        for _ in range(args.repeats):
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            s.step(args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            times.append(ev0.elapsed_time(ev1) / 1e3)
+    dt = float(np.median(times))
     s.check_finite()
     mass = s.mass()
     phi_now = s.fields()[0]
@@ -529,13 +737,7 @@ def run_cuda(args):
             sv.set_fields(phi)
             sv.step(args.warmup)
             torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sv.step(args.steps)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            dtv = e0.elapsed_time(e1) / 1e3
+            dtv = median_steps_time(sv, torch, stream, args.steps, args.repeats)
             lbv = time_lb_kernel(sv, torch, reps)
             lbytes = fluid * lb_bytes_fluid(st) + (N - fluid) * LB_BYTES_SOLID
             sv.check_finite()
@@ -547,6 +749,9 @@ def run_cuda(args):
                          "step_frac": N * step_bytes(st) * args.steps / dtv / 1e9 / peak}
             sv.close()
 
+    workloads = None
+    if not args.no_variants and world == 1:
+        workloads = paper_workloads(args, torch, cacl, stream)
     batched = None
     if not args.no_batch and world == 1:
         batched = run_batched(args, torch, cacl, stream)
@@ -563,7 +768,8 @@ def run_cuda(args):
                "sample": sample}
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup,
+        "steps": args.steps, "warmup": args.warmup, "repeats": args.repeats,
+        "repeat_ms": [round(x * 1e3, 4) for x in times],
         "ms_per_step": dt_max / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "storage": args.storage,
@@ -589,11 +795,12 @@ def run_cuda(args):
                           "ideal_mlups": peak * 1e9 / step_bytes(args.storage) / 1e6},
         "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": kernels_per_step * args.steps,
+        "gpu_launches": kernels_per_step * args.steps * args.repeats,
         "clocks": clk.summary(),
         "checks": {"mass_drift_rel": drift, "lambda": mass["lam"]},
         "cpu_baseline": cpu,
         "mixed": mixed or None,
+        "workloads": workloads,
         "batched": batched,
         "adjoint": adj,
     }
@@ -605,6 +812,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="timed repeats of --steps steps; the median is reported")
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--grid", type=int, default=GRID,
                     help="cube edge (the benchmark is 256; smaller edges are "
@@ -642,7 +851,22 @@ def main():
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint/forward cost measurement and "
                          "print its JSON (for profiling the adjoint kernels)")
+    ap.add_argument("--inference", action="store_true",
+                    help="run the wettability inference (96^3, 8x8 patches) instead")
+    ap.add_argument("--inf-steps", type=int, default=2000)
+    ap.add_argument("--inf-every", type=int, default=100)
+    ap.add_argument("--inf-iters", type=int, default=30)
+    ap.add_argument("--c2-accuracy", action="store_true",
+                    help="storage-mode error on the 128^3 spreading case "
+                         "against the FP64 oracle instead")
+    ap.add_argument("--c2-steps", type=int, default=60)
     args = ap.parse_args()
+    if args.inference:
+        run_inference(args)
+        return
+    if args.c2_accuracy:
+        run_c2_accuracy(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.theta_recovery:

@@ -261,7 +261,8 @@ __device__ __forceinline__ void node_store(IDX n, IDX N, const NodeOut<float>& o
 }
 
 // Everything after the pull and the phi stencil: the compressive vector
-// (written to a), the collision, and the stores of f*, u.
+// (written to a before the collision, so that it is not held across it),
+// the collision, and the stores of f*, u.
 template <typename Store, typename IDX>
 __device__ __forceinline__ void lb_finish(IDX n, IDX N, const float (&f)[Q],
                                           float phi0, float gx, float gy,
@@ -270,10 +271,19 @@ __device__ __forceinline__ void lb_finish(IDX n, IDX N, const float (&f)[Q],
                                           float* __restrict__ u,
                                           float* __restrict__ a,
                                           const Consts& k) {
-  NodeOut<float> o;
+  const float lap = lap_from_sum(phi0, ssum);
   float ax, ay, az;
-  node_eval(f, phi0, gx, gy, gz, ssum, k, o, ax, ay, az);
-  node_store<Store, IDX>(n, N, o, ax, ay, az, fout, u, a);
+  compressive(phi0, gx, gy, gz, ax, ay, az);
+  a[n] = ax;
+  a[N + n] = ay;
+  a[2 * N + n] = az;
+  NodeOut<float> o;
+  collide(f, phi0, gx, gy, gz, lap, k, o);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) fout[q * N + n] = Store::encode_w(o.P[q], q);
+  u[n] = o.ux;
+  u[N + n] = o.uy;
+  u[2 * N + n] = o.uz;
 }
 
 // Pull and phi stencil of the fluid node (x, y, z) of one grid, read from
@@ -343,39 +353,88 @@ __device__ __forceinline__ void lb_node(int x, int y, int z,
                                         float* __restrict__ a,
                                         const uint8_t* __restrict__ flags,
                                         const Grid& g, const Consts& k) {
-  NodeOut<float> o;
-  float ax, ay, az;
-  if (!lb_node_eval<Store, IDX>(x, y, z, fin, phi, flags, g, k, o, ax, ay, az))
-    return;
-  const IDX n = x + (IDX)g.nx * y + (IDX)g.nx * g.ny * z;
-  node_store<Store, IDX>(n, (IDX)g.N, o, ax, ay, az, fout, u, a);
+  const IDX nx = g.nx;
+  const IDX nxy = (IDX)g.nx * g.ny;
+  const IDX N = (IDX)g.N;
+  const IDX n = x + nx * y + nxy * z;
+  const uint8_t fl = flags[n];
+  if (fl & FLAG_SOLID) return;
+  const IDX xo[3] = {(IDX)wrap(x, -1, g.nx), (IDX)x, (IDX)wrap(x, 1, g.nx)};
+  const IDX yo[3] = {wrap(y, -1, g.ny) * nx, y * nx, wrap(y, 1, g.ny) * nx};
+  const IDX zo[3] = {wrap(z, -1, g.nz) * nxy, z * nxy, wrap(z, 1, g.nz) * nxy};
+  IDX yz[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) yz[b][c] = yo[b] + zo[c];
+
+  float f[Q];
+  if (fl & FLAG_NEAR) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const IDX src = xo[1 - cx(q)] + yz[1 - cy(q)][1 - cz(q)];
+      const bool bb = (q != REST) && (__ldg(flags + src) & FLAG_SOLID);
+      f[q] = Store::decode(bb ? __ldg(fin + (opp(q) * N + n)) : __ldg(fin + (q * N + src)), q);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const IDX src = xo[1 - cx(q)] + yz[1 - cy(q)][1 - cz(q)];
+      f[q] = Store::decode(__ldg(fin + (q * N + src)), q);
+    }
+  }
+
+  // isotropic gradient and Laplacian of phi (Eqs. grad_iso, lap_iso)
+  const float phi0 = __ldg(phi + n);
+  float gx = 0.f, gy = 0.f, gz = 0.f, ssum = 0.f;
+#pragma unroll
+  for (int q = 0; q < REST; ++q) {
+    const float vp = __ldg(phi + (xo[1 + cx(q)] + yz[1 + cy(q)][1 + cz(q)]));
+    const float vm = __ldg(phi + (xo[1 - cx(q)] + yz[1 - cy(q)][1 - cz(q)]));
+    stencil_pair(q, vp, vm, gx, gy, gz, ssum);
+  }
+  lb_finish<Store, IDX>(n, N, f, phi0, gx, gy, gz, ssum, fout, u, a, k);
 }
 
-// Evaluation of an x pair of fluid nodes (x0, x0 + 1) away from walls from
-// its 27 pulled population pairs and the 9 phi rows of its stencil, each
-// row given as (phi(x0 - 1), (phi(x0), phi(x0 + 1)), phi(x0 + 2)); rows
-// indexed [dy + 1][dz + 1]. Packed pair arithmetic, bit-identical to
-// node_eval on each node.
-__device__ __forceinline__ void pair_eval(const float2 (&f)[Q],
-                                          const float2 (&pc)[3][3],
-                                          const float (&pl)[3][3],
-                                          const float (&pr)[3][3],
-                                          const Consts& k, NodeOut<float2>& o,
-                                          float2& ax, float2& ay, float2& az) {
+// Isotropic gradient and neighbour sum (Eqs. grad_iso, lap_iso) of an x
+// pair of nodes (x0, x0 + 1) from the 9 phi rows of its stencil, each row
+// given as (phi(x0 - 1), (phi(x0), phi(x0 + 1)), phi(x0 + 2)), rows indexed
+// [dy + 1][dz + 1]; packed pair arithmetic, bit-identical to the one-node
+// stencil on each node.
+__device__ __forceinline__ void pair_stencil(const float2 (&pc)[3][3],
+                                             const float (&pl)[3][3],
+                                             const float (&pr)[3][3], float2& phi0,
+                                             float2& gx, float2& gy, float2& gz,
+                                             float2& ssum) {
   // phi at x + d for both nodes of the pair, d = -1, 0, +1
   auto shifted = [&](int b, int c, int d) {
     return d == 0 ? pc[b][c]
          : d > 0 ? make_float2(pc[b][c].y, pr[b][c])
                  : make_float2(pl[b][c], pc[b][c].x);
   };
-  const float2 phi0 = pc[1][1];
-  float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx, ssum = gx;
+  phi0 = pc[1][1];
+  gx = make_float2(0.f, 0.f);
+  gy = gx;
+  gz = gx;
+  ssum = gx;
 #pragma unroll
   for (int q = 0; q < REST; ++q) {
     const float2 vp = shifted(1 + cy(q), 1 + cz(q), cx(q));
     const float2 vm = shifted(1 - cy(q), 1 - cz(q), -cx(q));
     stencil_pair(q, vp, vm, gx, gy, gz, ssum);
   }
+}
+
+// The whole evaluation of such a pair (stencil, compressive vector,
+// collision) from its 27 pulled population pairs.
+__device__ __forceinline__ void pair_eval(const float2 (&f)[Q],
+                                          const float2 (&pc)[3][3],
+                                          const float (&pl)[3][3],
+                                          const float (&pr)[3][3],
+                                          const Consts& k, NodeOut<float2>& o,
+                                          float2& ax, float2& ay, float2& az) {
+  float2 phi0, gx, gy, gz, ssum;
+  pair_stencil(pc, pl, pr, phi0, gx, gy, gz, ssum);
   node_eval(f, phi0, gx, gy, gz, ssum, k, o, ax, ay, az);
 }
 
@@ -406,17 +465,22 @@ __device__ __forceinline__ void lb_pair(int x0, int y, int z,
   const int yo[3] = {wrap(y, -1, g.ny) * nx, y * nx, wrap(y, 1, g.ny) * nx};
   const int zo[3] = {wrap(z, -1, g.nz) * nxy, z * nxy, wrap(z, 1, g.nz) * nxy};
 
-  float2 pc[3][3];
-  float pl[3][3], pr[3][3];
+  // phi stencil first: its rows are dead before the populations arrive
+  float2 phi0, gx, gy, gz, ssum;
+  {
+    float2 pc[3][3];
+    float pl[3][3], pr[3][3];
 #pragma unroll
-  for (int b = 0; b < 3; ++b)
+    for (int b = 0; b < 3; ++b)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int row = yo[b] + zo[c];
-      pc[b][c] = __ldg(reinterpret_cast<const float2*>(phi + row + x0));
-      pl[b][c] = __ldg(phi + row + xl);
-      pr[b][c] = __ldg(phi + row + xr);
-    }
+      for (int c = 0; c < 3; ++c) {
+        const int row = yo[b] + zo[c];
+        pc[b][c] = __ldg(reinterpret_cast<const float2*>(phi + row + x0));
+        pl[b][c] = __ldg(phi + row + xl);
+        pr[b][c] = __ldg(phi + row + xr);
+      }
+    pair_stencil(pc, pl, pr, phi0, gx, gy, gz, ssum);
+  }
 
   // pulled populations f*_q(x - c_q) of both nodes
   float2 f[Q];
@@ -434,12 +498,13 @@ __device__ __forceinline__ void lb_pair(int x0, int y, int z,
     f[q] = Store::decode2(v, q);
   }
 
-  NodeOut<float2> o;
   float2 ax, ay, az;
-  pair_eval(f, pc, pl, pr, k, o, ax, ay, az);
+  compressive(phi0, gx, gy, gz, ax, ay, az);
   *reinterpret_cast<float2*>(a + n) = ax;
   *reinterpret_cast<float2*>(a + N + n) = ay;
   *reinterpret_cast<float2*>(a + 2 * N + n) = az;
+  NodeOut<float2> o;
+  collide(f, phi0, gx, gy, gz, lap_from_sum(phi0, ssum), k, o);
 #pragma unroll
   for (int q = 0; q < Q; ++q)
     *reinterpret_cast<T2*>(fout + q * N + n) = Store::encode_w2(o.P[q], q);
@@ -711,11 +776,13 @@ lb_collide(const typename Store::T* __restrict__ fin,
 // LB2_PY rows of one plane. A pair with a solid node or a wall neighbour
 // (bounce-back links) runs the one-node path for each of its nodes.
 template <typename Store>
-__global__ void __launch_bounds__(LB2_PX * LB2_PY)
-lb_collide_pair(const typename Store::T* __restrict__ fin,
-                typename Store::T* __restrict__ fout, const float* __restrict__ phi,
-                float* __restrict__ u, float* __restrict__ a,
-                const uint8_t* __restrict__ flags, Grid g, Consts k) {
+__device__ __forceinline__ void lb_pair_block(const typename Store::T* __restrict__ fin,
+                                              typename Store::T* __restrict__ fout,
+                                              const float* __restrict__ phi,
+                                              float* __restrict__ u,
+                                              float* __restrict__ a,
+                                              const uint8_t* __restrict__ flags,
+                                              const Grid& g, const Consts& k) {
   const int x0 = 2 * (blockIdx.x * LB2_PX + threadIdx.x);
   const int y = blockIdx.y * LB2_PY + threadIdx.y;
   const int z = blockIdx.z;
@@ -729,6 +796,26 @@ lb_collide_pair(const typename Store::T* __restrict__ fin,
     for (int j = 0; j < 2; ++j)
       lb_node<Store, int>(x0 + j, y, z, fin, fout, phi, u, a, flags, g, k);
   }
+}
+
+// FP32 populations: at most 96 registers (five blocks of 128 per SM, no
+// spills); 16-bit populations: the compiler's own choice (96, no spills).
+template <typename Store>
+__global__ void __launch_bounds__(LB2_PX * LB2_PY, 5)
+lb_collide_pair32(const typename Store::T* __restrict__ fin,
+                  typename Store::T* __restrict__ fout, const float* __restrict__ phi,
+                  float* __restrict__ u, float* __restrict__ a,
+                  const uint8_t* __restrict__ flags, Grid g, Consts k) {
+  lb_pair_block<Store>(fin, fout, phi, u, a, flags, g, k);
+}
+
+template <typename Store>
+__global__ void __launch_bounds__(LB2_PX * LB2_PY)
+lb_collide_pair16(const typename Store::T* __restrict__ fin,
+                  typename Store::T* __restrict__ fout, const float* __restrict__ phi,
+                  float* __restrict__ u, float* __restrict__ a,
+                  const uint8_t* __restrict__ flags, Grid g, Consts k) {
+  lb_pair_block<Store>(fin, fout, phi, u, a, flags, g, k);
 }
 
 // TMA-tiled collide-stream (CACL_OPT_LB_PIPE = 3). A tile is TX consecutive
@@ -1121,8 +1208,12 @@ void launch_store(cacl_ctx* c, const void* fin, void* fout, const float* phi) {
   if (lb_pair_ok(c, fin, fout, phi)) {
     dim3 block(LB2_PX, LB2_PY, 1);
     dim3 grid((g.nx / 2 + LB2_PX - 1) / LB2_PX, (g.ny + LB2_PY - 1) / LB2_PY, g.nz);
-    lb_collide_pair<Store><<<grid, block, 0, c->stream>>>(
-        (const T*)fin, (T*)fout, phi, c->u, c->a, c->flags, g, c->k);
+    if constexpr (sizeof(T) == 4)
+      lb_collide_pair32<Store><<<grid, block, 0, c->stream>>>(
+          (const T*)fin, (T*)fout, phi, c->u, c->a, c->flags, g, c->k);
+    else
+      lb_collide_pair16<Store><<<grid, block, 0, c->stream>>>(
+          (const T*)fin, (T*)fout, phi, c->u, c->a, c->flags, g, c->k);
     return;
   }
   dim3 block(LB_BX, LB_BY, 1);

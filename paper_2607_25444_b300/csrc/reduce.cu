@@ -49,13 +49,16 @@ correct_phi(float* __restrict__ phi, const uint8_t* __restrict__ flags,
     const uchar4 fl = *reinterpret_cast<const uchar4*>(flags + i4);
     float* pv = &v.x;
     const uint8_t fa[4] = {fl.x, fl.y, fl.z, fl.w};
+    bool band = false;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float s = pv[j];
-      const float chi = (s > eps && s < 1.0f - eps) ? s * (1.0f - s) : 0.0f;
-      if (!(fa[j] & FLAG_SOLID)) pv[j] = add_unbiased(s, lam * chi, step, i4 + j);
+      const bool in = (s > eps && s < 1.0f - eps) && !(fa[j] & FLAG_SOLID);
+      if (in) pv[j] = add_unbiased(s, lam * (s * (1.0f - s)), step, i4 + j);
+      band |= in;
     }
-    *reinterpret_cast<float4*>(phi + i4) = v;
+    // outside the interface band chi = 0 and phi is unchanged: no store
+    if (band) *reinterpret_cast<float4*>(phi + i4) = v;
   } else {
     for (int64_t n = i4; n < N; ++n) {
       const float s = phi[n];

@@ -95,6 +95,38 @@ def test_dtheta_directional_vs_oracle_fd(gpu_grad, seed):
     assert abs(ad - fd) <= 1e-3 * abs(fd), (ad, fd)
 
 
+def test_dtheta_every_wall_node_vs_fp64_cpu_adjoint(gpu_grad):
+    """The whole per-wall-node dL/dtheta vector and dL/dsigma against the
+    FP64 CPU adjoint (reverse mode of oracle/torch_step.py, which is pinned
+    to the C++ oracle's forward and to its central differences), with the
+    same rule for the compressive normal in the bulk phases: every one of
+    the wall nodes within 1e-3 of the largest entry, dL/dsigma within 1e-3
+    relative. 16 x 16 x 12, 20 steps, four contact-angle patches, density
+    ratio 2, gravity."""
+    import torch
+
+    from oracle import torch_step as TS
+    p, solid, phi, theta, patch, r = _case()
+    o = O.Oracle(p)
+    o.set_geometry(solid)
+    wall = o.wall_list()
+    assert np.array_equal(wall["idx"], gpu_grad["idx"])
+    ts = TS.TorchStep(p, solid, wall, frozen_bulk_normal=True)
+    th = torch.tensor(theta.reshape(-1)[wall["idx"]].astype(np.float64),
+                      requires_grad=True)
+    sg = torch.tensor(p["sigma"], dtype=torch.float64, requires_grad=True)
+    _, ph, _ = ts.rollout(phi.astype(np.float64), th, sg, STEPS)
+    (ph * torch.tensor(r.astype(np.float64))).sum().backward()
+    ref = th.grad.numpy()
+    got = gpu_grad["dtheta"]
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    print(f"dtheta per wall node: {ref.size} nodes, max |gpu - cpu| / max |cpu| {err:.2e}")
+    assert err < 1e-3, err
+    ds = abs(gpu_grad["dsigma"] - sg.grad.item()) / abs(sg.grad.item())
+    print(f"dsigma: gpu {gpu_grad['dsigma']:.9e} cpu {sg.grad.item():.9e} rel {ds:.2e}")
+    assert ds < 1e-3, ds
+
+
 def test_dsigma_vs_oracle_fd(gpu_grad):
     p, solid, phi, theta, patch, r = _case()
     h = 1e-6
