@@ -290,6 +290,65 @@ cacl_status cacl_get_info(const cacl_ctx* ctx, int64_t* nodes,
                           int64_t* device_bytes, int32_t* wall_count);
 
 /*
+ * z-slab decomposition: one problem split along z into slabs, one per GPU
+ * (or several on one GPU), each an ordinary context with two halo planes on
+ * each side. This is the parallel split of the step across devices that
+ * the paper's large domains call for: per step one exchange of phi before
+ * and after the ghost update, one of f* and of u, a after the
+ * collide-stream, and one gather of the phi update's block partial sums for
+ * the global volume correction (Sect. 2.3, Eqs. tentative_phase_field_mass
+ * .. mass_corrected_phi).
+ *
+ * cacl_slab_create: a slab owning global planes [z0, z0 + nz) of the grid
+ *   described by *global (0 <= z0, z0 + nz <= global->nz). Its context has
+ *   nz + 4 planes, periodic in z: local plane l holds global plane
+ *   z0 - 2 + l (wrapped around global->nz). Set its geometry, fields and
+ *   angles with the ordinary calls on those nz + 4 planes (halo planes
+ *   included), then set the global mass reference with cacl_set_mass_ref
+ *   (cacl_set_fields sums the slab's own planes only).
+ * cacl_slab_stage: one stage of the step on every local plane (ghost
+ *   update, collide-stream) or on the interior planes (phi update: block
+ *   partial sums only, no correction).
+ * cacl_slab_partials: the last phi update's block partial sums, nb phi*
+ *   sums then nb chi sums (device dst, 2 nb doubles; NULL dst queries nb).
+ *   Blocks are ordered by their z tile last, so the slabs' arrays in slab
+ *   order, phi* parts of all slabs first and then the chi parts, are the
+ *   undivided context's array when every interior starts on a multiple of
+ *   the phi update's tile depth (32 planes with the default tile).
+ * cacl_slab_correct: lambda from such a gathered array (device, nb_total
+ *   phi* sums then nb_total chi sums), in the fixed order an undivided
+ *   context uses, then the correction; the rounding key uses global node
+ *   indices.
+ * cacl_slab_halo: direction 0 packs the interior planes next to side 0
+ *   (low z) or 1 (high z) into buf, direction 1 unpacks buf into the halo
+ *   planes on that side. field CACL_SLAB_PHI: 2 planes of phi (ghosts
+ *   included); CACL_SLAB_F: 1 plane of the 27 current populations (storage
+ *   type); CACL_SLAB_UA: 1 plane of u (3 components) then a (3). buf is a
+ *   device buffer of cacl_slab_halo_bytes(ctx, field) bytes, component-major,
+ *   then plane, y, x. A slab's low interior planes feed the halo of the
+ *   slab below (its side 1) and its high ones the slab above (side 0).
+ * Enqueued on the context's stream; CACL_ERR_STATE on an ordinary context.
+ */
+enum {
+  CACL_SLAB_PHI = 0,
+  CACL_SLAB_F = 1,
+  CACL_SLAB_UA = 2
+};
+enum {
+  CACL_SLAB_GHOST = 0,
+  CACL_SLAB_COLLIDE = 1,
+  CACL_SLAB_PHASE = 2
+};
+cacl_status cacl_slab_create(const cacl_params* global, int z0, int nz,
+                             void* stream, cacl_ctx** out);
+cacl_status cacl_slab_stage(cacl_ctx* ctx, int stage);
+cacl_status cacl_slab_partials(cacl_ctx* ctx, double* dst, int* nblocks);
+cacl_status cacl_slab_correct(cacl_ctx* ctx, const double* all, int nb_total);
+cacl_status cacl_slab_halo(cacl_ctx* ctx, int field, int side, int direction,
+                           void* buf);
+int64_t cacl_slab_halo_bytes(const cacl_ctx* ctx, int field);
+
+/*
  * Allocation-free volume correction (the paper has no counterpart: this is
  * a library service). Some callers cannot call cudaMalloc: a process whose
  * device memory already belongs to another allocator's pool, a host that

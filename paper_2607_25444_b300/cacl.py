@@ -32,6 +32,8 @@ EXPORTS = (
     "cacl_batch_case", "cacl_batch_step", "cacl_batch_set_option",
     "cacl_batch_autotune", "cacl_set_wall_angles", "cacl_set_sigma",
     "cacl_adjoint_forward", "cacl_adjoint_forward_levels", "cacl_adjoint_backward",
+    "cacl_slab_create", "cacl_slab_stage", "cacl_slab_partials", "cacl_slab_correct",
+    "cacl_slab_halo", "cacl_slab_halo_bytes",
 )
 OPT_PHASE_TILE = 1
 OPT_PHASE_PIPE = 2  # 0 auto, 1 register staging, 2 asynchronous copies
@@ -113,11 +115,19 @@ def load():
     L.cacl_adjoint_forward.argtypes = [vp, C.c_int, C.c_int]
     L.cacl_adjoint_forward_levels.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     L.cacl_adjoint_backward.argtypes = [vp, vp, vp, vp]
+    L.cacl_slab_create.argtypes = [C.POINTER(CaclParams), C.c_int, C.c_int, vp,
+                                   C.POINTER(vp)]
+    L.cacl_slab_stage.argtypes = [vp, C.c_int]
+    L.cacl_slab_partials.argtypes = [vp, vp, C.POINTER(C.c_int)]
+    L.cacl_slab_correct.argtypes = [vp, vp, C.c_int]
+    L.cacl_slab_halo.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
+    L.cacl_slab_halo_bytes.argtypes = [vp, C.c_int]
     for name in EXPORTS:
         f = getattr(L, name)
         if name not in ("cacl_destroy", "cacl_last_error", "cacl_batch_destroy",
-                        "cacl_batch_last_error"):
+                        "cacl_batch_last_error", "cacl_slab_halo_bytes"):
             f.restype = C.c_int
+    L.cacl_slab_halo_bytes.restype = C.c_int64
     _lib = L
     return L
 
@@ -202,8 +212,16 @@ class Solver:
     two-dimensional problem is a periodic slab one node thick).
     """
 
-    def __init__(self, params, stream=None, handle=None):
+    def __init__(self, params, stream=None, handle=None, local_shape=None):
         self.L = load()
+        if handle is not None and local_shape is not None:
+            # a slab context (slab.SlabSolver): owned, local grid given
+            self.params = None
+            self.shape = tuple(int(v) for v in local_shape)
+            self.N = int(np.prod(self.shape))
+            self.h = C.c_void_p(handle)
+            self._owned = True
+            return
         if handle is not None:  # a case owned by a Batch
             self.params = dict(params)
             self.p = make_params(params)

@@ -418,6 +418,16 @@ struct cacl_ctx {
   CUtensorMap lbt_fload[2], lbt_fstore[2], lbt_phi[2], lbt_u, lbt_a;
   int phase_nblocks = 0;   // blocks of the last phase-update launch
 
+  // z slab of a decomposition (cacl_slab_create): the phi update covers
+  // planes [zbase, zlim) (zlim 0 = every plane), lambda is formed from
+  // gathered partials instead of by the phi update's last block, and the
+  // rounding key of the correction uses global node indices (node_offset
+  // added to the local index)
+  int zbase = 0, zlim = 0;
+  bool ext_finalize = false;
+  int64_t node_offset = 0;
+  int slab_z0 = 0, slab_nz = 0;  // first global plane and interior planes
+
   // reductions
   int part_blocks = 0;
   double* partials = nullptr;  // [2][part_blocks]
@@ -453,6 +463,7 @@ cudaError_t launch_compressive(cacl_ctx* c, const float* phi);
 cudaError_t phase_init_attributes();
 cudaError_t launch_phase(cacl_ctx* c, const float* phi_in, float* phi_out);
 cudaError_t launch_correct(cacl_ctx* c, float* phi);
+cudaError_t launch_mass_from(cacl_ctx* c, const double* partials, int nb);
 cudaError_t launch_mass_ref(cacl_ctx* c, const float* phi);
 cudaError_t launch_init_populations(cacl_ctx* c);
 cudaError_t launch_pstar(cacl_ctx* c, const void* f, float* out);

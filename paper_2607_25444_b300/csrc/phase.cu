@@ -300,10 +300,12 @@ __device__ __forceinline__ void block_partials(DF msum, DF wsum, int tid,
 
 // After the block's partial sums are stored: the last block of the launch
 // to finish (a ticket counter, no waiting) forms lambda from all partials
-// and resets the counter for the next launch.
+// and resets the counter for the next launch. Without a ticket (a slab of
+// a z decomposition) nothing is formed here.
 __device__ __forceinline__ void finish_mass(const double* partials, int nb,
                                             MassScalars* ms, unsigned* ticket,
                                             int tid) {
+  if (!ticket) return;  // the caller forms lambda from gathered partials
   __shared__ bool last;
   if (tid == 0) {
     __threadfence();  // this block's partials before its ticket
@@ -329,7 +331,8 @@ __device__ __forceinline__ void phase_tile_body(
     int bxi, int byi, int bzi, int pb, const float* __restrict__ phi,
     const float* __restrict__ afld, float* __restrict__ phi_out,
     const float* __restrict__ u, const uint8_t* __restrict__ flags,
-    double* __restrict__ partials, int nblocks, const Grid& g, const Consts& k) {
+    double* __restrict__ partials, int nblocks, const Grid& g, const Consts& k,
+    int zbase, int zlim) {
   constexpr int PX = TX + 4, PY = TY + 4, NP = PX * PY;  // phi plane, halo 2
   constexpr int AX = TX + 2, AY = TY + 2, NA = AX * AY;  // a plane, halo 1
   constexpr int THREADS = TX * TY / 2;
@@ -344,8 +347,8 @@ __device__ __forceinline__ void phase_tile_body(
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = tx + TX * ty;
-  const int x0 = bxi * TX, y0 = byi * TY, z0 = bzi * ZC;
-  const int zend = min(z0 + ZC, g.nz);
+  const int x0 = bxi * TX, y0 = byi * TY, z0 = zbase + bzi * ZC;
+  const int zend = min(z0 + ZC, zlim);
   const int nxy = g.nx * g.ny;
   const int64_t N = g.N;
 
@@ -571,7 +574,7 @@ __device__ __forceinline__ void phase_tile_copy(
     const float* __restrict__ afld, float* __restrict__ phi_out,
     const float* __restrict__ u, const uint8_t* __restrict__ flags,
     double* __restrict__ partials, int nblocks, const Grid& g, const Consts& k,
-    float* smem) {
+    float* smem, int zbase, int zlim) {
   using L = CopyTile<TY, D>;
   constexpr int THREADS = TX * TY / 2;
   static_assert(L::PR * NCH <= THREADS && L::AR * NCH <= THREADS &&
@@ -583,8 +586,8 @@ __device__ __forceinline__ void phase_tile_copy(
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = tx + TX * ty;
-  const int x0 = bxi * TX, y0 = byi * TY, z0 = bzi * ZC;
-  const int zend = min(z0 + ZC, g.nz);
+  const int x0 = bxi * TX, y0 = byi * TY, z0 = zbase + bzi * ZC;
+  const int zend = min(z0 + ZC, zlim);
   const int nxy = g.nx * g.ny;
   const int64_t N = g.N;
 
@@ -697,10 +700,10 @@ phase_update_march(const float* __restrict__ phi, const float* __restrict__ afld
                    float* __restrict__ phi_out, const float* __restrict__ u,
                    const uint8_t* __restrict__ flags,
                    double* __restrict__ partials, int nblocks, Grid g,
-                   Consts k, MassScalars* ms, unsigned* ticket) {
+                   Consts k, MassScalars* ms, unsigned* ticket, int zbase, int zlim) {
   const int pb = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   phase_tile_body<TY, ZC>(blockIdx.x, blockIdx.y, blockIdx.z, pb, phi, afld,
-                          phi_out, u, flags, partials, nblocks, g, k);
+                          phi_out, u, flags, partials, nblocks, g, k, zbase, zlim);
   finish_mass(partials, nblocks, ms, ticket, threadIdx.x + TX * threadIdx.y);
 }
 
@@ -710,11 +713,12 @@ phase_update_copy(const float* __restrict__ phi, const float* __restrict__ afld,
                   float* __restrict__ phi_out, const float* __restrict__ u,
                   const uint8_t* __restrict__ flags,
                   double* __restrict__ partials, int nblocks, Grid g,
-                  Consts k, MassScalars* ms, unsigned* ticket) {
+                  Consts k, MassScalars* ms, unsigned* ticket, int zbase, int zlim) {
   extern __shared__ __align__(16) float dsm[];
   const int pb = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   phase_tile_copy<TY, ZC, D>(blockIdx.x, blockIdx.y, blockIdx.z, pb, phi, afld,
-                             phi_out, u, flags, partials, nblocks, g, k, dsm);
+                             phi_out, u, flags, partials, nblocks, g, k, dsm, zbase,
+                             zlim);
   finish_mass(partials, nblocks, ms, ticket, threadIdx.x + TX * threadIdx.y);
 }
 
@@ -735,7 +739,8 @@ phase_update_batch(const CaseDesc* __restrict__ cases, WorkList wl, int pc) {
     __syncthreads();  // the previous tile's shared-memory reads are done
     phase_tile_body<TY, ZC>(local % nbx, (local / nbx) % nby, local / (nbx * nby),
                             local, cd.phi[pc], cd.a, cd.phi[1 - pc], cd.u,
-                            cd.flags, cd.partials, cd.phase_nb, cd.g, cd.k);
+                            cd.flags, cd.partials, cd.phase_nb, cd.g, cd.k, 0,
+                            cd.g.nz);
   }
 }
 
@@ -777,10 +782,9 @@ PhaseShape phase_shape(int variant) {
   }
 }
 
-dim3 phase_grid(const Grid& g, int variant) {
+dim3 phase_grid(const Grid& g, int variant, int nzr) {
   const PhaseShape s = phase_shape(variant);
-  return dim3((g.nx + TX - 1) / TX, (g.ny + s.ty - 1) / s.ty,
-              (g.nz + s.zc - 1) / s.zc);
+  return dim3((g.nx + TX - 1) / TX, (g.ny + s.ty - 1) / s.ty, (nzr + s.zc - 1) / s.zc);
 }
 
 }  // namespace
@@ -789,7 +793,7 @@ int phase_blocks(const cacl_ctx* c) {
   // partial-sum storage is sized for the variant with the most blocks
   int nb = 0;
   for (int v = 0; v < 4; ++v) {
-    const dim3 gr = phase_grid(c->g, v);
+    const dim3 gr = phase_grid(c->g, v, c->g.nz);
     nb = std::max(nb, (int)(gr.x * gr.y * gr.z));
   }
   return nb;
@@ -834,7 +838,7 @@ phase_update_batch_copy(const CaseDesc* __restrict__ cases, WorkList wl, int pc)
     phase_tile_copy<TY, ZC, COPY_D>(local % nbx, (local / nbx) % nby,
                                     local / (nbx * nby), local, cd.phi[pc], cd.a,
                                     cd.phi[1 - pc], cd.u, cd.flags, cd.partials,
-                                    cd.phase_nb, cd.g, cd.k, dsm);
+                                    cd.phase_nb, cd.g, cd.k, dsm, 0, cd.g.nz);
   }
 }
 
@@ -922,14 +926,18 @@ cudaError_t launch_compressive(cacl_ctx* c, const float* phi) {
   return cudaGetLastError();
 }
 
+// The phi update over planes [zbase, zlim) of the context (every plane for
+// an ordinary context, the interior planes of a slab).
 cudaError_t launch_phase(cacl_ctx* c, const float* phi_in, float* phi_out) {
   const int v = c->phase_variant;
-  const dim3 grid = phase_grid(c->g, v);
+  const int zbase = c->zbase, zlim = c->zlim > 0 ? c->zlim : c->g.nz;
+  const dim3 grid = phase_grid(c->g, v, zlim - zbase);
   const int nb = (int)(grid.x * grid.y * grid.z);
   c->phase_nblocks = nb;
   const PhaseShape s = phase_shape(v);
   const dim3 block(TX, s.ty / 2, 1);
   const bool copy_ok = phase_copy_ok(c->g, phi_in, phi_out, c->a, c->u, c->flags);
+  unsigned* ticket = c->ext_finalize ? nullptr : c->ticket;
   if (c->phase_pipe == 2 && !copy_ok) return cudaErrorInvalidValue;
   if (c->phase_pipe != 1 && copy_ok) {
     const CopyKernel ck = copy_kernel(v);
@@ -941,33 +949,33 @@ cudaError_t launch_phase(cacl_ctx* c, const float* phi_in, float* phi_out) {
     Consts k = c->k;
     int nbk = nb;
     MassScalars* ms = c->mass;
-    unsigned* ticket = c->ticket;
+    int zb = zbase, zl = zlim;
     void* args[] = {(void*)&phi_in, (void*)&a,    (void*)&phi_out,
                     (void*)&u,      (void*)&fl,   (void*)&part,
                     (void*)&nbk,    (void*)&g,    (void*)&k,
-                    (void*)&ms,     (void*)&ticket};
+                    (void*)&ms,     (void*)&ticket, (void*)&zb, (void*)&zl};
     return cudaLaunchKernel(ck.fn, grid, block, args, ck.smem, c->stream);
   }
   switch (v) {
     case 1:
       phase_update_march<8, 16, 4><<<grid, block, 0, c->stream>>>(
           phi_in, c->a, phi_out, c->u, c->flags, c->partials, nb, c->g, c->k,
-          c->mass, c->ticket);
+          c->mass, ticket, zbase, zlim);
       break;
     case 2:
       phase_update_march<8, 32, 4><<<grid, block, 0, c->stream>>>(
           phi_in, c->a, phi_out, c->u, c->flags, c->partials, nb, c->g, c->k,
-          c->mass, c->ticket);
+          c->mass, ticket, zbase, zlim);
       break;
     case 3:
       phase_update_march<16, 32, 2><<<grid, block, 0, c->stream>>>(
           phi_in, c->a, phi_out, c->u, c->flags, c->partials, nb, c->g, c->k,
-          c->mass, c->ticket);
+          c->mass, ticket, zbase, zlim);
       break;
     default:
       phase_update_march<16, 16, 2><<<grid, block, 0, c->stream>>>(
           phi_in, c->a, phi_out, c->u, c->flags, c->partials, nb, c->g, c->k,
-          c->mass, c->ticket);
+          c->mass, ticket, zbase, zlim);
       break;
   }
   return cudaGetLastError();

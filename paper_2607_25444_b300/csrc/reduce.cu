@@ -40,7 +40,8 @@ finalize_mass_batch(const CaseDesc* __restrict__ cases) {
 // rounded without bias.
 __global__ void __launch_bounds__(ELEM_THREADS)
 correct_phi(float* __restrict__ phi, const uint8_t* __restrict__ flags,
-            const MassScalars* __restrict__ ms, int64_t N, float eps) {
+            const MassScalars* __restrict__ ms, int64_t N, float eps,
+            int64_t node_offset) {
   const float lam = ms->lambda_f;
   const uint32_t step = ms->step;
   const int64_t i4 = ((int64_t)blockIdx.x * ELEM_THREADS + threadIdx.x) * 4;
@@ -54,7 +55,7 @@ correct_phi(float* __restrict__ phi, const uint8_t* __restrict__ flags,
     for (int j = 0; j < 4; ++j) {
       const float s = pv[j];
       const bool in = (s > eps && s < 1.0f - eps) && !(fa[j] & FLAG_SOLID);
-      if (in) pv[j] = add_unbiased(s, lam * (s * (1.0f - s)), step, i4 + j);
+      if (in) pv[j] = add_unbiased(s, lam * (s * (1.0f - s)), step, node_offset + i4 + j);
       band |= in;
     }
     // outside the interface band chi = 0 and phi is unchanged: no store
@@ -63,7 +64,7 @@ correct_phi(float* __restrict__ phi, const uint8_t* __restrict__ flags,
     for (int64_t n = i4; n < N; ++n) {
       const float s = phi[n];
       const float chi = (s > eps && s < 1.0f - eps) ? s * (1.0f - s) : 0.0f;
-      if (!(flags[n] & FLAG_SOLID)) phi[n] = add_unbiased(s, lam * chi, step, n);
+      if (!(flags[n] & FLAG_SOLID)) phi[n] = add_unbiased(s, lam * chi, step, node_offset + n);
     }
   }
 }
@@ -200,7 +201,19 @@ cudaError_t launch_correct(cacl_ctx* c, float* phi) {
   const int64_t N = c->g.N;
   const int nb = (int)((N + 4 * ELEM_THREADS - 1) / (4 * ELEM_THREADS));
   correct_phi<<<nb, ELEM_THREADS, 0, c->stream>>>(phi, c->flags, c->mass, N,
-                                                 c->k.eps_phi);
+                                                 c->k.eps_phi, c->node_offset);
+  return cudaGetLastError();
+}
+
+// lambda from partial sums gathered by the caller (nb phi* sums, then nb
+// chi sums), in the fixed order of the phi update's own finalize.
+__global__ void __launch_bounds__(32)
+finalize_mass_from(const double* __restrict__ partials, int nb, MassScalars* ms) {
+  mass_from_partials(partials, nb, ms, threadIdx.x);
+}
+
+cudaError_t launch_mass_from(cacl_ctx* c, const double* partials, int nb) {
+  finalize_mass_from<<<1, 32, 0, c->stream>>>(partials, nb, c->mass);
   return cudaGetLastError();
 }
 
