@@ -32,14 +32,18 @@ import numpy as np  # noqa: E402
 GRID = 256
 THETA = 60.0
 METRIC = "MLUPS (CAC-LB step, 256^3)"
-STORE_BYTES = {"f32": 4, "f16": 2, "bf16": 2}
+STORE_BYTES = {"f32": 4, "f16": 2, "bf16": 2, "moments": 4}
+# values stored per node for the populations: 27 populations, or the 17
+# coefficients of the moment form
+STORE_COMPS = {"f32": 27, "f16": 27, "bf16": 27, "moments": 17}
 LB_BYTES_SOLID = 1
 
 
 def lb_bytes_fluid(storage="f32"):
     """Algorithmic bytes of the collide-stream per fluid node: 27 populations
-    read + written, phi read, u written (3 x FP32), flags read."""
-    return 27 * STORE_BYTES[storage] * 2 + 4 + 12 + 1
+    (17 coefficients in moment form) read + written, phi read, u written
+    (3 x FP32), flags read."""
+    return STORE_COMPS[storage] * STORE_BYTES[storage] * 2 + 4 + 12 + 1
 
 
 def step_bytes(storage="f32"):
@@ -730,7 +734,7 @@ def run_cuda(args):
     # the same workload with 16-bit population storage (FP32 arithmetic)
     mixed = {}
     if args.storage == "f32" and not args.no_variants:
-        for st in ("f16", "bf16"):
+        for st in ("f16", "bf16", "moments"):
             pv = dict(p, storage=st)
             sv = cacl.Solver(pv)
             sv.set_geometry(solid)
@@ -818,7 +822,7 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID,
                     help="cube edge (the benchmark is 256; smaller edges are "
                          "for profiling captures)")
-    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "moments"],
                     help="population storage of the headline line")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the adjoint/forward cost measurement")

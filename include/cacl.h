@@ -56,11 +56,23 @@ typedef enum {
                               allocation-free entry point */
 } cacl_status;
 
-/* Storage of the populations; arithmetic is FP32 in every mode. */
+/* Storage of the populations; arithmetic is FP32 in every mode.
+ *   CACL_F32           the 27 post-collision populations f*_q, FP32
+ *   CACL_F16_SHIFTED   h_q = (f*_q - w_q p*_ref) / w_q with p*_ref = 0,
+ *   CACL_BF16_SHIFTED  rounded to FP16 / BF16 (nearest even)
+ *   CACL_F32_MOMENTS   the paper's thread-safe moment form (Sect. 2.1): each
+ *                      node keeps the 17 coefficients of its post-collision
+ *                      polynomial P (f*_q = w_q P(c_q)) in FP32, and the
+ *                      collide-stream rebuilds the populations it pulls from
+ *                      the neighbours' coefficients; bit-identical to
+ *                      CACL_F32 at fluid nodes from a state at rest. Not
+ *                      available to cacl_set_populations, the adjoint or
+ *                      batches. */
 typedef enum {
   CACL_F32 = 0,
   CACL_F16_SHIFTED = 1,
-  CACL_BF16_SHIFTED = 2
+  CACL_BF16_SHIFTED = 2,
+  CACL_F32_MOMENTS = 3
 } cacl_storage;
 
 /*

@@ -18,7 +18,7 @@ STATUS = {0: "CACL_OK", -1: "CACL_ERR_ARG", -2: "CACL_ERR_CUDA",
           -3: "CACL_ERR_STATE", -4: "CACL_ERR_GEOMETRY",
           -5: "CACL_ERR_DIVERGED", -6: "CACL_ERR_TIMEOUT",
           -7: "CACL_ERR_TOO_LARGE"}
-STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2, "moments": 3}
 
 EXPORTS = (
     "cacl_create", "cacl_destroy", "cacl_last_error", "cacl_set_geometry",

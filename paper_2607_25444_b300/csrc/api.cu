@@ -115,7 +115,7 @@ cacl_status cacl_create(const cacl_params* p, void* stream, cacl_ctx** out) {
       !(p->eps_phi > 0 && p->eps_phi < 0.5) || !(p->sigma >= 0))
     return CACL_ERR_ARG;
   if (p->storage != CACL_F32 && p->storage != CACL_F16_SHIFTED &&
-      p->storage != CACL_BF16_SHIFTED)
+      p->storage != CACL_BF16_SHIFTED && p->storage != CACL_F32_MOMENTS)
     return CACL_ERR_ARG;
   cacl_ctx* c = new cacl_ctx();
   c->p = *p;
@@ -150,7 +150,7 @@ cacl_status cacl_create(const cacl_params* p, void* stream, cacl_ctx** out) {
   }
   if ((e = phase_init_attributes()) != cudaSuccess) return bail("attributes");
   if ((e = lb_init(c)) != cudaSuccess) return bail("collide-stream set-up");
-  const size_t fbytes = storage_bytes(p->storage) * (size_t)Q * N;
+  const size_t fbytes = storage_bytes(p->storage) * (size_t)pop_comps(p->storage) * N;
   for (int i = 0; i < 2; ++i) {
     if ((e = cudaMalloc(&c->f[i], fbytes)) != cudaSuccess) return bail("alloc f");
     if ((e = cudaMalloc(&c->phi[i], sizeof(float) * N)) != cudaSuccess)
@@ -279,7 +279,10 @@ cacl_status cacl_set_fields(cacl_ctx* c, const float* phi, const float* u) {
   else
     CK(cudaMemsetAsync(c->u, 0, sizeof(float) * 3 * N, c->stream), "zero u");
   CK(cudaMemsetAsync(c->a, 0, sizeof(float) * 3 * N, c->stream), "zero a");
-  CK(launch_init_populations(c), "init populations");
+  if (c->p.storage == CACL_F32_MOMENTS)
+    CK(launch_moments_init(c), "init moments");
+  else
+    CK(launch_init_populations(c), "init populations");
   CK(launch_mass_ref(c, c->phi[0]), "mass reference");
   CK(cudaStreamSynchronize(c->stream), "sync");
   c->fcur = 0;
@@ -291,6 +294,9 @@ cacl_status cacl_set_fields(cacl_ctx* c, const float* phi, const float* u) {
 cacl_status cacl_set_populations(cacl_ctx* c, const float* f) {
   if (!c || !f) return fail(c, CACL_ERR_ARG, "null argument");
   if (!ready(c)) return CACL_ERR_STATE;
+  if (c->p.storage == CACL_F32_MOMENTS)
+    return fail(c, CACL_ERR_ARG, "the moment form holds 17 coefficients per node, "
+                                 "not arbitrary populations");
   const size_t bytes = sizeof(float) * Q * c->g.N;
   if (c->p.storage == CACL_F32) {
     CK(cudaMemcpyAsync(c->f[c->fcur], f, bytes, cudaMemcpyHostToDevice,
@@ -386,12 +392,17 @@ cacl_status cacl_get_fields(cacl_ctx* c, float* phi, float* u, float* pstar,
        "copy phi");
   if (u) CK(cudaMemcpyAsync(u, c->u, sizeof(float) * 3 * N, kind, c->stream), "copy u");
   if (pstar) {
+    auto pst = [&](float* dst) {
+      return c->p.storage == CACL_F32_MOMENTS
+                 ? launch_moments_expand(c, c->f[c->fcur], nullptr, dst)
+                 : launch_pstar(c, c->f[c->fcur], dst);
+    };
     if (device_ptrs) {
-      CK(launch_pstar(c, c->f[c->fcur], pstar), "p*");
+      CK(pst(pstar), "p*");
     } else {
       float* tmp = nullptr;
       CK(cudaMalloc(&tmp, sizeof(float) * N), "alloc p*");
-      cudaError_t e = launch_pstar(c, c->f[c->fcur], tmp);
+      cudaError_t e = pst(tmp);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(pstar, tmp, sizeof(float) * N,
                             cudaMemcpyDeviceToHost, c->stream);
@@ -413,11 +424,16 @@ cacl_status cacl_get_populations(cacl_ctx* c, float* f, int device_ptrs) {
                        device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        c->stream), "copy f");
   } else if (device_ptrs) {
-    CK(launch_from_storage(c, c->f[c->fcur], f), "decode f");
+    if (c->p.storage == CACL_F32_MOMENTS)
+      CK(launch_moments_expand(c, c->f[c->fcur], f, nullptr), "expand moments");
+    else
+      CK(launch_from_storage(c, c->f[c->fcur], f), "decode f");
   } else {
     float* tmp = nullptr;
     CK(cudaMalloc(&tmp, bytes), "alloc f staging");
-    cudaError_t e = launch_from_storage(c, c->f[c->fcur], tmp);
+    cudaError_t e = c->p.storage == CACL_F32_MOMENTS
+                        ? launch_moments_expand(c, c->f[c->fcur], tmp, nullptr)
+                        : launch_from_storage(c, c->f[c->fcur], tmp);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(f, tmp, bytes, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -498,6 +514,8 @@ cacl_status cacl_set_option(cacl_ctx* c, int option, int value) {
   }
   if (option == CACL_OPT_LB_PIPE) {
     if (value < 0 || value > 3) return fail(c, CACL_ERR_ARG, "unknown collide pipeline");
+    if (value != 0 && c->p.storage == CACL_F32_MOMENTS)
+      return fail(c, CACL_ERR_ARG, "the moment form has one collide-stream kernel");
     const int pf = 16 / (int)storage_bytes(c->p.storage);
     if (value == 1 && (c->g.nx % pf != 0 || c->g.nx % 4 != 0))
       return fail(c, CACL_ERR_ARG, "staged collide-stream needs nx a multiple of 16 bytes");

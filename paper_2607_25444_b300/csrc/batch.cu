@@ -189,6 +189,7 @@ cacl_status cacl_batch_create(const cacl_params* params, int ncases,
   *out = nullptr;
   for (int i = 1; i < ncases; ++i)
     if (params[i].storage != params[0].storage) return CACL_ERR_ARG;
+  if (params[0].storage == CACL_F32_MOMENTS) return CACL_ERR_ARG;  // population forms only
   cacl_batch* b = new cacl_batch();
   b->storage = params[0].storage;
   if (stream) {

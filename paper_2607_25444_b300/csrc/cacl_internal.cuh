@@ -108,7 +108,12 @@ struct StoreBF16 {
   __device__ __forceinline__ static T hi(T2 v) { return __high2bfloat16(v); }
 };
 
-inline size_t storage_bytes(int storage) { return storage == CACL_F32 ? 4 : 2; }
+inline size_t storage_bytes(int storage) {
+  return (storage == CACL_F32 || storage == CACL_F32_MOMENTS) ? 4 : 2;
+}
+// components per node of the population buffers: 27 populations, or the 17
+// coefficients of the moment form
+inline int pop_comps(int storage) { return storage == CACL_F32_MOMENTS ? 17 : 27; }
 
 // Node flags (one byte per node).
 constexpr uint8_t FLAG_SOLID = 1;  // node is solid
@@ -466,6 +471,8 @@ cudaError_t launch_correct(cacl_ctx* c, float* phi);
 cudaError_t launch_mass_from(cacl_ctx* c, const double* partials, int nb);
 cudaError_t launch_mass_ref(cacl_ctx* c, const float* phi);
 cudaError_t launch_init_populations(cacl_ctx* c);
+cudaError_t launch_moments_init(cacl_ctx* c);
+cudaError_t launch_moments_expand(cacl_ctx* c, const void* C, float* f, float* pstar);
 cudaError_t launch_pstar(cacl_ctx* c, const void* f, float* out);
 cudaError_t launch_to_storage(cacl_ctx* c, const float* src, void* dst);
 cudaError_t launch_from_storage(cacl_ctx* c, const void* src, float* dst);

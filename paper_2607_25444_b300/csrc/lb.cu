@@ -60,10 +60,54 @@ struct NodeOut {
   V ux, uy, uz;
 };
 
+// The 17 coefficients of the post-collision polynomial P in the separable
+// monomials (the node's post-collision state in moment form), in storage
+// order: 1; c_x, c_y, c_z; e_x, e_y, e_z; c_x c_y, c_x c_z, c_y c_z;
+// e_x c_y, e_x c_z, e_y c_x, e_y c_z, e_z c_x, e_z c_y; c_x c_y c_z.
+constexpr int NCOEF = 17;
 template <typename V>
-__device__ __forceinline__ void collide(const V (&f)[Q], V phi0, V gx, V gy,
-                                        V gz, V lap, const Consts& k,
-                                        NodeOut<V>& o) {
+struct Coefs {
+  V k1, Lx, Ly, Lz, Dx, Dy, Dz, Fxy, Fxz, Fyz, Mxy, Mxz, Myx, Myz, Mzx, Mzy, X;
+};
+
+// P at all 27 velocities from the coefficients: three one-axis transforms
+// (z, then y, then x: g(0) = g_1, g(+-1) = g_1 + g_e +- g_c).
+template <typename V>
+__device__ __forceinline__ void coefs_to_P(const Coefs<V>& c, V (&P)[Q]) {
+  // z transform: Z_ij(cz) for x basis i, y basis j (1, c, e); index cz+1
+  V Z00[3], Z10[3], Z20[3], Z01[3], Z11[3], Z02[3];
+  {
+    const V t00 = vadd(c.k1, c.Dz), t10 = vadd(c.Lx, c.Mzx), t01 = vadd(c.Ly, c.Mzy);
+    Z00[0] = vsub(t00, c.Lz); Z00[1] = c.k1; Z00[2] = vadd(t00, c.Lz);
+    Z10[0] = vsub(t10, c.Fxz); Z10[1] = c.Lx; Z10[2] = vadd(t10, c.Fxz);
+    Z20[0] = vsub(c.Dx, c.Mxz); Z20[1] = c.Dx; Z20[2] = vadd(c.Dx, c.Mxz);
+    Z01[0] = vsub(t01, c.Fyz); Z01[1] = c.Ly; Z01[2] = vadd(t01, c.Fyz);
+    Z11[0] = vsub(c.Fxy, c.X); Z11[1] = c.Fxy; Z11[2] = vadd(c.Fxy, c.X);
+    Z02[0] = vsub(c.Dy, c.Myz); Z02[1] = c.Dy; Z02[2] = vadd(c.Dy, c.Myz);
+  }
+  // y transform then x transform, line by line (cy, cz)
+#pragma unroll
+  for (int kz = 0; kz < 3; ++kz) {
+    const V t0 = vadd(Z00[kz], Z02[kz]), t1 = vadd(Z10[kz], c.Myx);
+    const V Y0[3] = {vsub(t0, Z01[kz]), Z00[kz], vadd(t0, Z01[kz])};
+    const V Y1[3] = {vsub(t1, Z11[kz]), Z10[kz], vadd(t1, Z11[kz])};
+    const V Y2[3] = {vsub(Z20[kz], c.Mxy), Z20[kz], vadd(Z20[kz], c.Mxy)};
+#pragma unroll
+    for (int jy = 0; jy < 3; ++jy) {
+      const int q = 9 * kz + 3 * jy;
+      const V t = vadd(Y0[jy], Y2[jy]);
+      P[q] = vsub(t, Y1[jy]);
+      P[q + 1] = Y0[jy];
+      P[q + 2] = vadd(t, Y1[jy]);
+    }
+  }
+}
+
+// The collision up to the coefficients of P (and u).
+template <typename V>
+__device__ __forceinline__ void collide_coefs(const V (&f)[Q], V phi0, V gx, V gy,
+                                              V gz, V lap, const Consts& k,
+                                              Coefs<V>& cf, V& uxo, V& uyo, V& uzo) {
   // moments by sum factorisation: along x for each (cy, cz) line l, then
   // along y for each cz, then along z (q = 9 (cz+1) + 3 (cy+1) + (cx+1))
   V m0[9], m1[9], m2[9];  // sum f, sum cx f, sum cx^2 f over the line
@@ -194,36 +238,23 @@ __device__ __forceinline__ void collide(const V (&f)[Q], V phi0, V gx, V gy,
   const V X = vfma(om6, dot3(ux, Ayz, uy, Axz, uz, Axy),
                    vmul(vmul(vmul(C(27.0f), ux), uy), uz));
 
-  // z transform: Z_ij(cz) for x basis i, y basis j (1, c, e); index cz+1
-  V Z00[3], Z10[3], Z20[3], Z01[3], Z11[3], Z02[3];
-  {
-    const V t00 = vadd(k1, Dz), t10 = vadd(Lx, Mzx), t01 = vadd(Ly, Mzy);
-    Z00[0] = vsub(t00, Lz); Z00[1] = k1; Z00[2] = vadd(t00, Lz);
-    Z10[0] = vsub(t10, Fxz); Z10[1] = Lx; Z10[2] = vadd(t10, Fxz);
-    Z20[0] = vsub(Dx, Mxz); Z20[1] = Dx; Z20[2] = vadd(Dx, Mxz);
-    Z01[0] = vsub(t01, Fyz); Z01[1] = Ly; Z01[2] = vadd(t01, Fyz);
-    Z11[0] = vsub(Fxy, X); Z11[1] = Fxy; Z11[2] = vadd(Fxy, X);
-    Z02[0] = vsub(Dy, Myz); Z02[1] = Dy; Z02[2] = vadd(Dy, Myz);
-  }
-  // y transform then x transform, line by line (cy, cz)
-#pragma unroll
-  for (int kz = 0; kz < 3; ++kz) {
-    const V t0 = vadd(Z00[kz], Z02[kz]), t1 = vadd(Z10[kz], Myx);
-    const V Y0[3] = {vsub(t0, Z01[kz]), Z00[kz], vadd(t0, Z01[kz])};
-    const V Y1[3] = {vsub(t1, Z11[kz]), Z10[kz], vadd(t1, Z11[kz])};
-    const V Y2[3] = {vsub(Z20[kz], Mxy), Z20[kz], vadd(Z20[kz], Mxy)};
-#pragma unroll
-    for (int jy = 0; jy < 3; ++jy) {
-      const int q = 9 * kz + 3 * jy;
-      const V t = vadd(Y0[jy], Y2[jy]);
-      o.P[q] = vsub(t, Y1[jy]);
-      o.P[q + 1] = Y0[jy];
-      o.P[q + 2] = vadd(t, Y1[jy]);
-    }
-  }
-  o.ux = ux;
-  o.uy = uy;
-  o.uz = uz;
+  cf.k1 = k1; cf.Lx = Lx; cf.Ly = Ly; cf.Lz = Lz;
+  cf.Dx = Dx; cf.Dy = Dy; cf.Dz = Dz;
+  cf.Fxy = Fxy; cf.Fxz = Fxz; cf.Fyz = Fyz;
+  cf.Mxy = Mxy; cf.Mxz = Mxz; cf.Myx = Myx; cf.Myz = Myz; cf.Mzx = Mzx; cf.Mzy = Mzy;
+  cf.X = X;
+  uxo = ux;
+  uyo = uy;
+  uzo = uz;
+}
+
+template <typename V>
+__device__ __forceinline__ void collide(const V (&f)[Q], V phi0, V gx, V gy,
+                                        V gz, V lap, const Consts& k,
+                                        NodeOut<V>& o) {
+  Coefs<V> cf;
+  collide_coefs(f, phi0, gx, gy, gz, lap, k, cf, o.ux, o.uy, o.uz);
+  coefs_to_P(cf, o.P);
 }
 
 // Laplacian of Eq. lap_iso from the neighbour sum: 6 (ssum - (1 - w_0) phi).
@@ -1051,6 +1082,249 @@ lb_collide_tma(const __grid_constant__ LbTmaArgs m,
   }
 }
 
+// Collide-stream in moment form (storage CACL_F32_MOMENTS): a node stores
+// the 17 coefficients of its post-collision polynomial P instead of its 27
+// populations, f*_q = w_q P(c_q) (the paper's thread-safe form, in which a
+// node keeps macroscopic moments and its neighbours rebuild the pulled
+// populations, Sect. 2.1). A block owns a MX x MY column of nodes and
+// marches up MZC planes. For each plane z' it rebuilds, for the column and
+// a one-node halo in x and y, every node's 27 populations from its
+// coefficients with the transforms of the collision and keeps them in
+// shared memory by the plane that pulls them: those with c_z = +1 for
+// plane z' + 1 (a ring of three planes), c_z = 0 for z' (two) and c_z = -1
+// for z' - 1 (one). Plane z then pulls f_q from the node x - c_q of the
+// right slot; the values are the very numbers the population form would
+// have stored (same transform, same w_q rounding), so the two forms are
+// bit-identical at fluid nodes. Near a wall the bounced-back populations
+// come from the node's own coefficients. The collision writes the 17
+// coefficients, u and a.
+constexpr int MX = 32, MY = 8, MZC = 16;
+constexpr int MHX = MX + 2, MHY = MY + 2, MNH = MHX * MHY;  // halo tile
+
+struct MomentSmem {
+  float sp[3][9][MNH];  // c_z = +1 populations of plane z' (ring by z' mod 3)
+  float s0[2][9][MNH];  // c_z = 0 (ring by z' mod 2)
+  float sm[9][MNH];     // c_z = -1 of the plane above the one computed
+};
+
+__device__ __forceinline__ void load_coefs(const float* __restrict__ C, int64_t n,
+                                           int64_t N, Coefs<float>& c) {
+  c.k1 = __ldg(C + n);
+  c.Lx = __ldg(C + N + n);
+  c.Ly = __ldg(C + 2 * N + n);
+  c.Lz = __ldg(C + 3 * N + n);
+  c.Dx = __ldg(C + 4 * N + n);
+  c.Dy = __ldg(C + 5 * N + n);
+  c.Dz = __ldg(C + 6 * N + n);
+  c.Fxy = __ldg(C + 7 * N + n);
+  c.Fxz = __ldg(C + 8 * N + n);
+  c.Fyz = __ldg(C + 9 * N + n);
+  c.Mxy = __ldg(C + 10 * N + n);
+  c.Mxz = __ldg(C + 11 * N + n);
+  c.Myx = __ldg(C + 12 * N + n);
+  c.Myz = __ldg(C + 13 * N + n);
+  c.Mzx = __ldg(C + 14 * N + n);
+  c.Mzy = __ldg(C + 15 * N + n);
+  c.X = __ldg(C + 16 * N + n);
+}
+
+__device__ __forceinline__ void store_coefs(float* __restrict__ C, int64_t n, int64_t N,
+                                            const Coefs<float>& c) {
+  C[n] = c.k1;
+  C[N + n] = c.Lx;
+  C[2 * N + n] = c.Ly;
+  C[3 * N + n] = c.Lz;
+  C[4 * N + n] = c.Dx;
+  C[5 * N + n] = c.Dy;
+  C[6 * N + n] = c.Dz;
+  C[7 * N + n] = c.Fxy;
+  C[8 * N + n] = c.Fxz;
+  C[9 * N + n] = c.Fyz;
+  C[10 * N + n] = c.Mxy;
+  C[11 * N + n] = c.Mxz;
+  C[12 * N + n] = c.Myx;
+  C[13 * N + n] = c.Myz;
+  C[14 * N + n] = c.Mzx;
+  C[15 * N + n] = c.Mzy;
+  C[16 * N + n] = c.X;
+}
+
+// f*_q = w_q P(c_q) of one node from its coefficients (the population
+// form's stored value)
+__device__ __forceinline__ void coefs_to_pops(const Coefs<float>& c, float (&f)[Q]) {
+  float P[Q];
+  coefs_to_P(c, P);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) f[q] = StoreF32::encode_w(P[q], q);
+}
+
+__global__ void __launch_bounds__(MX * MY)
+lb_collide_moments(const float* __restrict__ Cin, float* __restrict__ Cout,
+                   const float* __restrict__ phi, float* __restrict__ u,
+                   float* __restrict__ a, const uint8_t* __restrict__ flags, Grid g,
+                   Consts k) {
+  extern __shared__ __align__(16) float msm[];
+  MomentSmem& sh = *reinterpret_cast<MomentSmem*>(msm);
+  const int tid = threadIdx.x;
+  const int tx = tid % MX, ty = tid / MX;
+  const int x0 = blockIdx.x * MX, y0 = blockIdx.y * MY, z0 = blockIdx.z * MZC;
+  const int z1 = min(z0 + MZC, g.nz);
+  const int64_t N = g.N;
+  const int64_t nxy = (int64_t)g.nx * g.ny;
+
+  // the halo nodes this thread rebuilds (at most two of MNH)
+  int hcol[2];
+  bool hact[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int h = tid + r * MX * MY;
+    hact[r] = h < MNH;
+    const int hx = h % MHX, hy = h / MHX;
+    hcol[r] = ((x0 - 1 + hx) % g.nx + g.nx) % g.nx +
+              g.nx * (((y0 - 1 + hy) % g.ny + g.ny) % g.ny);
+  }
+  auto rebuild = [&](int zp) {  // plane zp (any integer, wrapped)
+    const int zw = ((zp % g.nz) + g.nz) % g.nz;
+    const int sp = ((zp % 3) + 3) % 3, s0 = zp & 1;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (!hact[r]) continue;
+      const int h = tid + r * MX * MY;
+      Coefs<float> c;
+      load_coefs(Cin, hcol[r] + zw * nxy, N, c);
+      float f[Q];
+      coefs_to_pops(c, f);
+#pragma unroll
+      for (int j = 0; j < 9; ++j) {
+        sh.sm[j][h] = f[j];
+        sh.s0[s0][j][h] = f[9 + j];
+        sh.sp[sp][j][h] = f[18 + j];
+      }
+    }
+  };
+
+  rebuild(z0 - 1);
+  __syncthreads();
+  rebuild(z0);
+  const int x = x0 + tx, y = y0 + ty;
+  const bool act = x < g.nx && y < g.ny;
+  const int hme = (ty + 1) * MHX + (tx + 1);
+  for (int z = z0; z < z1; ++z) {
+    __syncthreads();  // every thread is done with the slots rebuilt below
+    rebuild(z + 1);
+    __syncthreads();
+    if (!act) continue;
+    const int64_t n = x + (int64_t)g.nx * y + nxy * z;
+    const uint8_t fl = flags[n];
+    if (fl & FLAG_SOLID) continue;
+    const int spm = (((z - 1) % 3) + 3) % 3, s0c = z & 1;
+    float f[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int h = hme - cy(q) * MHX - cx(q);
+      const int j = q % 9;
+      f[q] = cz(q) > 0 ? sh.sp[spm][j][h] : (cz(q) == 0 ? sh.s0[s0c][j][h] : sh.sm[j][h]);
+    }
+    const int xo[3] = {wrap(x, -1, g.nx), x, wrap(x, 1, g.nx)};
+    const int64_t yo[3] = {(int64_t)wrap(y, -1, g.ny) * g.nx, (int64_t)y * g.nx,
+                           (int64_t)wrap(y, 1, g.ny) * g.nx};
+    const int64_t zo[3] = {wrap(z, -1, g.nz) * nxy, z * nxy, wrap(z, 1, g.nz) * nxy};
+    if (fl & FLAG_NEAR) {
+      // halfway bounce-back: f_q = f*_{opp q}(x) of the previous step
+      Coefs<float> own;
+      load_coefs(Cin, n, N, own);
+      float fo[Q];
+      coefs_to_pops(own, fo);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        if (q == REST) continue;
+        const int64_t src = xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)];
+        if (__ldg(flags + src) & FLAG_SOLID) f[q] = fo[opp(q)];
+      }
+    }
+    // isotropic gradient and Laplacian of phi (Eqs. grad_iso, lap_iso)
+    const float phi0 = __ldg(phi + n);
+    float gx = 0.f, gy = 0.f, gz = 0.f, ssum = 0.f;
+#pragma unroll
+    for (int q = 0; q < REST; ++q) {
+      const float vp = __ldg(phi + (xo[1 + cx(q)] + yo[1 + cy(q)] + zo[1 + cz(q)]));
+      const float vm = __ldg(phi + (xo[1 - cx(q)] + yo[1 - cy(q)] + zo[1 - cz(q)]));
+      stencil_pair(q, vp, vm, gx, gy, gz, ssum);
+    }
+    const float lap = lap_from_sum(phi0, ssum);
+    float ax, ay, az;
+    compressive(phi0, gx, gy, gz, ax, ay, az);
+    a[n] = ax;
+    a[N + n] = ay;
+    a[2 * N + n] = az;
+    Coefs<float> cf;
+    float ux, uy, uz;
+    collide_coefs(f, phi0, gx, gy, gz, lap, k, cf, ux, uy, uz);
+    store_coefs(Cout, n, N, cf);
+    u[n] = ux;
+    u[N + n] = uy;
+    u[2 * N + n] = uz;
+  }
+}
+
+// Populations (27 N, FP32) of every node from the moment form, and p*.
+__global__ void __launch_bounds__(256)
+moments_to_pops(const float* __restrict__ C, float* __restrict__ f,
+                float* __restrict__ pstar, const uint8_t* __restrict__ flags, int64_t N) {
+  const int64_t n = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (n >= N) return;
+  Coefs<float> c;
+  load_coefs(C, n, N, c);
+  float v[Q];
+  coefs_to_pops(c, v);
+  if (f) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) f[q * N + n] = v[q];
+  }
+  if (pstar) {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) s += v[q];
+    pstar[n] = (flags[n] & FLAG_SOLID) ? 0.f : s;
+  }
+}
+
+// Equilibrium f^eq(p* = 0, u) in moment form (u = 0 at solid nodes): the
+// coefficients of Eq. feq3 with no non-equilibrium part and no force.
+__global__ void __launch_bounds__(256)
+moments_init(float* __restrict__ C0, float* __restrict__ C1, float* __restrict__ u,
+             const uint8_t* __restrict__ flags, int64_t N) {
+  const int64_t n = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (n >= N) return;
+  float ux = u[n], uy = u[N + n], uz = u[2 * N + n];
+  if (flags[n] & FLAG_SOLID) {
+    ux = uy = uz = 0.f;
+    u[n] = u[N + n] = u[2 * N + n] = 0.f;
+  }
+  const float uu = ux * ux + uy * uy + uz * uz;
+  const float k2 = 3.0f - 4.5f * uu;
+  Coefs<float> c;
+  c.k1 = -1.5f * uu;
+  c.Lx = ux * (k2 + 4.5f * ux * ux);
+  c.Ly = uy * (k2 + 4.5f * uy * uy);
+  c.Lz = uz * (k2 + 4.5f * uz * uz);
+  c.Dx = 4.5f * ux * ux;
+  c.Dy = 4.5f * uy * uy;
+  c.Dz = 4.5f * uz * uz;
+  c.Fxy = 9.0f * ux * uy;
+  c.Fxz = 9.0f * ux * uz;
+  c.Fyz = 9.0f * uy * uz;
+  c.Mxy = 13.5f * ux * ux * uy;
+  c.Mxz = 13.5f * ux * ux * uz;
+  c.Myx = 13.5f * uy * uy * ux;
+  c.Myz = 13.5f * uy * uy * uz;
+  c.Mzx = 13.5f * uz * uz * ux;
+  c.Mzy = 13.5f * uz * uz * uy;
+  c.X = 27.0f * ux * uy * uz;
+  store_coefs(C0, n, N, c);
+  store_coefs(C1, n, N, c);
+}
+
 // Batched collide-stream: virtual block b of the work-list is row block
 // (bx, y, z) of its case; rows of BX threads along x. Blocks stride through
 // the work-list (b, b + gridDim.x, ...) so that the rows in flight at any
@@ -1231,6 +1505,10 @@ void launch_store(cacl_ctx* c, const void* fin, void* fout, const float* phi) {
 // Resident-sized grid of the persistent copy-staged collide-stream (and its
 // shared-memory attribute), set once per context outside any graph capture.
 cudaError_t lb_init(cacl_ctx* c) {
+  if (c->p.storage == CACL_F32_MOMENTS)
+    return cudaFuncSetAttribute(lb_collide_moments,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(MomentSmem));
   switch (c->p.storage) {
     case CACL_F16_SHIFTED: return staged_setup<StoreF16>(c->g, &c->lb_grid);
     case CACL_BF16_SHIFTED: return staged_setup<StoreBF16>(c->g, &c->lb_grid);
@@ -1241,6 +1519,7 @@ cudaError_t lb_init(cacl_ctx* c) {
 // Tensor maps of the TMA-tiled collide-stream over the context's own
 // buffers (set once the buffers exist, outside any graph capture).
 cudaError_t lb_tma_init(cacl_ctx* c) {
+  if (c->p.storage == CACL_F32_MOMENTS) return cudaSuccess;  // not applicable
   switch (c->p.storage) {
     case CACL_F16_SHIFTED: return tma_setup<StoreF16>(c);
     case CACL_BF16_SHIFTED: return tma_setup<StoreBF16>(c);
@@ -1285,11 +1564,31 @@ bool lb_pair_ok(const cacl_ctx* c, const void* fin, const void* fout,
 
 cudaError_t launch_lb(cacl_ctx* c, const void* fin, void* fout,
                       const float* phi) {
+  if (c->p.storage == CACL_F32_MOMENTS) {
+    const Grid g = c->g;
+    const dim3 grid((g.nx + MX - 1) / MX, (g.ny + MY - 1) / MY, (g.nz + MZC - 1) / MZC);
+    lb_collide_moments<<<grid, MX * MY, sizeof(MomentSmem), c->stream>>>(
+        (const float*)fin, (float*)fout, phi, c->u, c->a, c->flags, g, c->k);
+    return cudaGetLastError();
+  }
   switch (c->p.storage) {
     case CACL_F16_SHIFTED: launch_store<StoreF16>(c, fin, fout, phi); break;
     case CACL_BF16_SHIFTED: launch_store<StoreBF16>(c, fin, fout, phi); break;
     default: launch_store<StoreF32>(c, fin, fout, phi); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments_init(cacl_ctx* c) {
+  const int nb = (int)((c->g.N + 255) / 256);
+  moments_init<<<nb, 256, 0, c->stream>>>((float*)c->f[0], (float*)c->f[1], c->u,
+                                          c->flags, c->g.N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments_expand(cacl_ctx* c, const void* C, float* f, float* pstar) {
+  const int nb = (int)((c->g.N + 255) / 256);
+  moments_to_pops<<<nb, 256, 0, c->stream>>>((const float*)C, f, pstar, c->flags, c->g.N);
   return cudaGetLastError();
 }
 

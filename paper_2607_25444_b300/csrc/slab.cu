@@ -39,7 +39,11 @@ cacl_status sfail(cacl_ctx* c, cacl_status st, const char* m) {
 void field_shape(const cacl_ctx* c, int field, int& planes, int& comps, size_t& esize) {
   switch (field) {
     case CACL_SLAB_PHI: planes = 2; comps = 1; esize = 4; break;
-    case CACL_SLAB_F: planes = 1; comps = Q; esize = storage_bytes(c->p.storage); break;
+    case CACL_SLAB_F:
+      planes = 1;
+      comps = pop_comps(c->p.storage);
+      esize = storage_bytes(c->p.storage);
+      break;
     default: planes = 1; comps = 6; esize = 4; break;  // u (3), a (3)
   }
 }
