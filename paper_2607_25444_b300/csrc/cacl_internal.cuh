@@ -459,6 +459,8 @@ bool lb_staged_ok(const cacl_ctx* c, const void* fin, const void* fout,
                   const void* phi);
 bool lb_pair_ok(const cacl_ctx* c, const void* fin, const void* fout,
                 const void* phi);
+bool lb_quad_ok(const cacl_ctx* c, const void* fin, const void* fout,
+                const void* phi);
 cudaError_t lb_tma_init(cacl_ctx* c);
 bool lb_tma_ok(const cacl_ctx* c, const void* fin, const void* fout,
                const void* phi);
