@@ -215,6 +215,11 @@ cacl_status cacl_check_finite(cacl_ctx* ctx);
 cacl_status cacl_adjoint_forward(cacl_ctx* ctx, int nsteps, int ckpt_every);
 cacl_status cacl_adjoint_backward(cacl_ctx* ctx, const float* dL_dphi,
                                   double* dL_dtheta, double* dL_dsigma);
+/* GPU time (CUDA events) of the last cacl_adjoint_backward: the taped
+ * recomputes of its segments (and outer segments) and the whole call, in
+ * milliseconds. CACL_ERR_STATE before any backward. */
+cacl_status cacl_adjoint_timing(const cacl_ctx* ctx, double* recompute_ms,
+                                double* total_ms);
 
 /* Two-level checkpointing for long rollouts: as cacl_adjoint_forward, but
  * the forward keeps a checkpoint only every outer_every steps (a positive

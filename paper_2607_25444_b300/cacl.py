@@ -32,7 +32,7 @@ EXPORTS = (
     "cacl_batch_case", "cacl_batch_step", "cacl_batch_set_option",
     "cacl_batch_autotune", "cacl_set_wall_angles", "cacl_set_sigma",
     "cacl_adjoint_forward", "cacl_adjoint_forward_levels", "cacl_adjoint_backward",
-    "cacl_slab_create", "cacl_slab_stage", "cacl_slab_partials", "cacl_slab_correct",
+    "cacl_adjoint_timing", "cacl_slab_create", "cacl_slab_stage", "cacl_slab_partials", "cacl_slab_correct",
     "cacl_slab_halo", "cacl_slab_halo_bytes",
 )
 OPT_PHASE_TILE = 1
@@ -115,6 +115,7 @@ def load():
     L.cacl_adjoint_forward.argtypes = [vp, C.c_int, C.c_int]
     L.cacl_adjoint_forward_levels.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     L.cacl_adjoint_backward.argtypes = [vp, vp, vp, vp]
+    L.cacl_adjoint_timing.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.cacl_slab_create.argtypes = [C.POINTER(CaclParams), C.c_int, C.c_int, vp,
                                    C.POINTER(vp)]
     L.cacl_slab_stage.argtypes = [vp, C.c_int]
@@ -371,6 +372,12 @@ class Solver:
         self._check(self.L.cacl_adjoint_backward(
             self.h, C.c_void_p(dl_dphi.data_ptr()), C.c_void_p(dl_dtheta.data_ptr()),
             C.c_void_p(dl_dsigma.data_ptr())))
+
+    def adjoint_timing(self):
+        """GPU milliseconds of the last backward: (recompute, total)."""
+        r, t = C.c_double(), C.c_double()
+        self._check(self.L.cacl_adjoint_timing(self.h, C.byref(r), C.byref(t)))
+        return r.value, t.value
 
     def set_option(self, option, value):
         self._check(self.L.cacl_set_option(self.h, int(option), int(value)))

@@ -505,7 +505,7 @@ __device__ __forceinline__ double block128_sum(double v, double* sh4) {
 
 // Per fluid node: the collision recomputed from the taped pull and reversed.
 // Block = 128 nodes of one x row (blockIdx.y = y, blockIdx.z = z); the
-// block's dL/dsigma share goes to partial[block].
+// block's dL/dsigma share is added to sig_acc[block].
 // The adjoint of the node's post-collision populations f*_q(n) is gathered
 // from the pulled-population adjoints of the later step (finb_later, or
 // zero when null) through the transpose of the pull: f*_q(n) fed
@@ -517,7 +517,7 @@ adj_lb_node(const float* __restrict__ fprev, const float* __restrict__ phig,
             const uint8_t* __restrict__ flags, const float* __restrict__ finb_later,
             const float* __restrict__ ub, const float* __restrict__ acb,
             float* __restrict__ finb, float* __restrict__ nodeb,
-            double* __restrict__ partial, Grid g, Consts k, float dbeta4_dsigma,
+            double* __restrict__ sig_acc, Grid g, Consts k, float dbeta4_dsigma,
             float dkphi_dsigma) {
   __shared__ double sh4[4];
   const int x = blockIdx.x * 128 + threadIdx.x;
@@ -573,8 +573,10 @@ adj_lb_node(const float* __restrict__ fprev, const float* __restrict__ phig,
     for (int c = 0; c < 5; ++c) nodeb[c * N + n] = 0.f;
   }
   const double tot = block128_sum(sig, sh4);
+  // each block owns one accumulator slot: the steps add to it in turn and
+  // the slots are summed once after the last step
   if (threadIdx.x == 0)
-    partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = tot;
+    sig_acc[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] += tot;
 }
 
 // Transpose of the phi stencil (gradient, Laplacian, own value) of the
@@ -675,12 +677,37 @@ __global__ void __launch_bounds__(AT)
 adj_ghost_gather(const uint8_t* __restrict__ flags, const float* __restrict__ phigb,
                  const int32_t* __restrict__ row_start,
                  const int32_t* __restrict__ row_entry,
-                 const float* __restrict__ wd, float* __restrict__ phib, int64_t N) {
+                 const float* __restrict__ wd, float* __restrict__ phib, int64_t N,
+                 const float* __restrict__ phis_next, float eps,
+                 double* __restrict__ partial) {
+  __shared__ double sh[AT / 32];
   const int64_t n = (int64_t)blockIdx.x * AT + threadIdx.x;
-  if (n >= N) return;
-  float v = (flags[n] & FLAG_WALL) ? 0.f : phigb[n];
-  for (int e = row_start[n]; e < row_start[n + 1]; ++e) v += wd[row_entry[e]];
-  phib[n] = v;
+  double s = 0.0;
+  if (n < N) {
+    const uint8_t fl = flags[n];
+    float v = (fl & FLAG_WALL) ? 0.f : phigb[n];
+    for (int e = row_start[n]; e < row_start[n + 1]; ++e) v += wd[row_entry[e]];
+    phib[n] = v;
+    // the next (earlier) step's correction adjoint needs S = sum over fluid
+    // of phi_bar chi(phi*): its block partial, formed here (adj_correct_sum
+    // on its own otherwise)
+    if (phis_next && !(fl & FLAG_SOLID)) {
+      const float w = phis_next[n];
+      const float chi = (w > eps && w < 1.f - eps) ? w * (1.f - w) : 0.f;
+      s = (double)v * (double)chi;
+    }
+  }
+  if (!phis_next) return;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int i = 0; i < AT / 32; ++i) t += sh[i];
+    partial[blockIdx.x] = t;
+  }
 }
 
 __global__ void __launch_bounds__(128)
@@ -726,6 +753,10 @@ struct AdjointState {
         *phigb = nullptr, *ub = nullptr, *ab = nullptr, *face = nullptr,
         *nodeb = nullptr, *wd = nullptr;
   double *thetab = nullptr, *sigmab = nullptr, *partial = nullptr;
+  double* sig_acc = nullptr;  // per-block dL/dsigma, summed after the last step
+  // GPU time of the last backward: the taped recomputes of the segments
+  // (and of the outer segments with two levels) and the whole call
+  double t_recompute_ms = 0.0, t_total_ms = 0.0;
   float* scal = nullptr;  // S / W and lambda of the correction adjoint
   int npart = 0;
   int32_t *row_start = nullptr, *row_entry = nullptr;
@@ -740,7 +771,7 @@ void adjoint_free(AdjointState* s) {
     for (float* p : *v) cudaFree(p);
   void* bufs[] = {s->ck_mass, s->ck1_mass, s->t_mass, s->fb, s->fb2, s->phib, s->phisb, s->phigb, s->ub,
                   s->ab, s->face, s->nodeb, s->wd, s->thetab, s->sigmab,
-                  s->partial, s->scal, s->row_start, s->row_entry};
+                  s->partial, s->sig_acc, s->scal, s->row_start, s->row_entry};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete s;
@@ -924,6 +955,7 @@ cacl_status cacl_adjoint_forward_levels(cacl_ctx* c, int nsteps, int every,
     ACK(alloc(&s->sigmab, 1), "alloc adjoint");
     s->npart = std::max((int)(((c->g.nx + 127) / 128) * (int64_t)c->g.ny * c->g.nz), 1024);
     ACK(alloc(&s->partial, s->npart), "alloc adjoint");
+    ACK(alloc(&s->sig_acc, s->npart), "alloc adjoint");
     ACK(alloc(&s->scal, 2), "alloc adjoint");
     const cacl_status st = build_transpose(c, s);
     if (st != CACL_OK) return st;
@@ -974,10 +1006,20 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
                       st), "save");
   ACK(cudaStreamSynchronize(st), "sync");
 
+  // events bracketing the recomputes and the whole call (timing only; the
+  // synchronisation after each recompute keeps the host in step)
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_0 = nullptr;
+  ACK(cudaEventCreate(&ev_a), "event");
+  ACK(cudaEventCreate(&ev_b), "event");
+  ACK(cudaEventCreate(&ev_0), "event");
+  s->t_recompute_ms = 0.0;
+  ACK(cudaEventRecord(ev_0, st), "event");
   ACK(cudaMemcpyAsync(s->phib, dL_dphi, sizeof(float) * N, cudaMemcpyDeviceToDevice, st),
       "seed");
   ACK(cudaMemsetAsync(s->thetab, 0, sizeof(double) * (W > 0 ? W : 1), st), "seed");
   ACK(cudaMemsetAsync(s->sigmab, 0, sizeof(double), st), "seed");
+  const int nbl_all = (int)(((g.nx + 127) / 128) * (int64_t)g.ny * g.nz);
+  ACK(cudaMemsetAsync(s->sig_acc, 0, sizeof(double) * nbl_all, st), "seed");
 
   const bool small = (int64_t)Q * N < (int64_t)INT32_MAX;  // 32-bit offsets
   const bool small15 = (int64_t)15 * N < (int64_t)INT32_MAX;  // face buffer
@@ -991,6 +1033,7 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
     const int m0 = J * span;                          // first step of the segment
     const int mlen = std::min(span, s->nsteps - m0);  // its steps
     if (s->outer > 0) {
+      ACK(cudaEventRecord(ev_a, st), "event");
       ACK(cudaMemcpyAsync(c->f[c->fcur], s->ck1_f[J], sizeof(float) * Q * N,
                           cudaMemcpyDeviceToDevice, st), "restore");
       ACK(cudaMemcpyAsync(c->phi[c->pcur], s->ck1_phi[J], sizeof(float) * N,
@@ -1007,6 +1050,11 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
         const cacl_status r = cacl_step(c, 1);
         if (r != CACL_OK) return r;
       }
+      ACK(cudaEventRecord(ev_b, st), "event");
+      ACK(cudaEventSynchronize(ev_b), "event");
+      float ms = 0.f;
+      ACK(cudaEventElapsedTime(&ms, ev_a, ev_b), "event");
+      s->t_recompute_ms += ms;
     }
     const int nseg = (mlen + s->every - 1) / s->every;
     for (int seg = nseg - 1; seg >= 0; --seg) {
@@ -1019,16 +1067,26 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
                           cudaMemcpyDeviceToDevice, st), "restore");
       ACK(cudaMemcpyAsync(c->mass, s->ck_mass + seg, sizeof(MassScalars),
                           cudaMemcpyDeviceToDevice, st), "restore");
+      ACK(cudaEventRecord(ev_a, st), "event");
       for (int t = 0; t < len; ++t) {
         const cacl_status r = taped_step(c, s, t, len);
         if (r != CACL_OK) return r;
       }
+      ACK(cudaEventRecord(ev_b, st), "event");
+      ACK(cudaEventSynchronize(ev_b), "event");
+      float ms = 0.f;
+      ACK(cudaEventElapsedTime(&ms, ev_a, ev_b), "event");
+      s->t_recompute_ms += ms;
       for (int t = len - 1; t >= 0; --t) {
-        // A1 correction
-        const int nb_sum = std::min(nblk(N, AT), 1024);
-        adj_correct_sum<<<nb_sum, AT, 0, st>>>(s->phib, s->t_phis[t], c->flags, N, eps,
-                                               s->partial);
-        adj_correct_scalars<<<1, 32, 0, st>>>(s->partial, nb_sum, s->t_mass + t, s->scal);
+        // A1 correction; S was summed by the ghost gather of the step after
+        // this one within the segment, else here
+        int nparts = nblk(N, AT);
+        if (t == len - 1) {
+          nparts = std::min(nblk(N, AT), 1024);
+          adj_correct_sum<<<nparts, AT, 0, st>>>(s->phib, s->t_phis[t], c->flags, N, eps,
+                                                 s->partial);
+        }
+        adj_correct_scalars<<<1, 32, 0, st>>>(s->partial, nparts, s->t_mass + t, s->scal);
         adj_correct_apply<<<nblk(N, AT), AT, 0, st>>>(s->phib, s->t_phis[t], c->flags,
                                                       N, eps, s->scal, s->phisb);
         // A2 phi update
@@ -1046,21 +1104,19 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
                                                           c->k);
         }
         // A3 collide-stream
-        const int nbl = (int)(rows.x * rows.y * rows.z);
         // the later step's pulled-population adjoints (none after the last)
         const float* later = first ? nullptr : s->fb;
         if (small) {
           adj_lb_node<int><<<rows, 128, 0, st>>>(s->t_fprev[t], s->t_phig[t], c->flags,
                                                  later, s->ub, s->ab, s->fb2, s->nodeb,
-                                                 s->partial, g, c->k, db4, dkp);
+                                                 s->sig_acc, g, c->k, db4, dkp);
         } else {
           adj_lb_node<int64_t><<<rows, 128, 0, st>>>(
               s->t_fprev[t], s->t_phig[t], c->flags, later, s->ub, s->ab, s->fb2,
-              s->nodeb, s->partial, g, c->k, db4, dkp);
+              s->nodeb, s->sig_acc, g, c->k, db4, dkp);
         }
         std::swap(s->fb, s->fb2);  // fb: this step's pulled-population adjoints
         first = false;
-        sum_partials<<<1, 128, 0, st>>>(s->partial, nbl, s->sigmab);
         if (small)
           adj_lb_gather<int><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
         else
@@ -1070,12 +1126,15 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
           adj_ghost_node<<<nblk(W, 128), 128, 0, st>>>(
               s->t_phipre[t], c->w_idx, c->w_donor, c->w_q, c->w_nw, c->w_cot,
               c->w_theta, s->phigb, s->wd, s->thetab, W, g);
-        adj_ghost_gather<<<nblk(N, AT), AT, 0, st>>>(c->flags, s->phigb, s->row_start,
-                                                     s->row_entry, s->wd, s->phib, N);
+        adj_ghost_gather<<<nblk(N, AT), AT, 0, st>>>(
+            c->flags, s->phigb, s->row_start, s->row_entry, s->wd, s->phib, N,
+            t > 0 ? s->t_phis[t - 1] : nullptr, eps, s->partial);
         ACK(cudaGetLastError(), "adjoint step");
       }
     }
   }
+  sum_partials<<<1, 128, 0, st>>>(s->sig_acc, nbl_all, s->sigmab);
+  ACK(cudaGetLastError(), "dsigma sum");
   if (dL_dtheta && W > 0)
     ACK(cudaMemcpyAsync(dL_dtheta, s->thetab, sizeof(double) * W,
                         cudaMemcpyDeviceToDevice, st), "copy dtheta");
@@ -1091,9 +1150,24 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
                       cudaMemcpyDeviceToDevice, st), "restore");
   ACK(cudaMemcpyAsync(c->mass, &save_mass, sizeof(MassScalars), cudaMemcpyHostToDevice,
                       st), "restore");
+  ACK(cudaEventRecord(ev_b, st), "event");
   ACK(cudaStreamSynchronize(st), "sync");
+  float tot = 0.f;
+  ACK(cudaEventElapsedTime(&tot, ev_0, ev_b), "event");
+  s->t_total_ms = tot;
+  cudaEventDestroy(ev_a);
+  cudaEventDestroy(ev_b);
+  cudaEventDestroy(ev_0);
   cudaFree(save_f);
   cudaFree(save_phi);
+  return CACL_OK;
+}
+
+cacl_status cacl_adjoint_timing(const cacl_ctx* c, double* recompute_ms,
+                                double* total_ms) {
+  if (!c || !c->adj) return CACL_ERR_STATE;
+  if (recompute_ms) *recompute_ms = c->adj->t_recompute_ms;
+  if (total_ms) *total_ms = c->adj->t_total_ms;
   return CACL_OK;
 }
 
