@@ -67,12 +67,12 @@ def workload(grid=GRID, theta=THETA):
 
 
 def kernel_traffic(fluid_nodes):
-    """DRAM bytes per collide-stream launch from the committed ncu summary,
-    scaled by fluid nodes; None when the kernel source changed since the
-    capture (its hash no longer matches)."""
+    """DRAM bytes per collide-stream launch from the committed ncu summary
+    (a full-size capture, in bytes per fluid node); None when the kernel
+    source changed since the capture (its hash no longer matches)."""
     import hashlib
     import re
-    prof = os.path.join(ROOT, "profiles", "lb_collide_f32_static_droplet_128cube.md")
+    prof = os.path.join(ROOT, "profiles", "lb_collide_pair32_static_droplet_256cube.md")
     if not os.path.exists(prof):
         return None
     text = open(prof).read()
@@ -793,7 +793,7 @@ def run_cuda(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "traffic": kernel_traffic(fluid) if args.storage == "f32" else None,
-                     "kernel": "lb_collide_f32",
+                     "kernel": "lb_collide_pair32" if args.storage == "f32" else "lb_collide",
                      "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": lb_bytes,
                      "kernel_bytes_per_fluid_node": lb_bytes_fluid(args.storage) + 12,
@@ -868,12 +868,23 @@ def main():
                     help="storage-mode error on the 128^3 spreading case "
                          "against the FP64 oracle instead")
     ap.add_argument("--c2-steps", type=int, default=60)
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched impact sweep and print its JSON")
     args = ap.parse_args()
     if args.inference:
         run_inference(args)
         return
     if args.c2_accuracy:
         run_c2_accuracy(args)
+        return
+    if args.batch_only:
+        import torch
+
+        from paper_2607_25444_b300 import cacl
+        torch.cuda.set_device(0)
+        torch.cuda.set_stream(torch.cuda.Stream())
+        print(json.dumps(run_batched(args, torch, cacl, torch.cuda.current_stream())),
+              flush=True)
         return
     if args.warmup < 3:
         args.warmup = 3
