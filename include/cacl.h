@@ -53,7 +53,8 @@ typedef enum {
   CACL_ERR_TIMEOUT = -6,   /* a bounded device wait gave up (reported by
                               cacl_check_finite) */
   CACL_ERR_TOO_LARGE = -7  /* size above the fixed scratch of an
-                              allocation-free entry point */
+                              allocation-free entry point, or above the
+                              32-bit indexing of a batch */
 } cacl_status;
 
 /* Storage of the populations; arithmetic is FP32 in every mode.
@@ -248,7 +249,9 @@ cacl_status cacl_adjoint_forward_levels(cacl_ctx* ctx, int nsteps,
  */
 typedef struct cacl_batch cacl_batch;
 
-/* ncases >= 1 parameter sets (same storage); stream as for cacl_create. */
+/* ncases >= 1 parameter sets (same storage, not CACL_F32_MOMENTS); stream
+ * as for cacl_create. CACL_ERR_TOO_LARGE when a case has 27 nx ny nz >=
+ * 2^31 nodes (the batched kernels index with 32 bits). */
 cacl_status cacl_batch_create(const cacl_params* params, int ncases,
                               void* stream, cacl_batch** out);
 void cacl_batch_destroy(cacl_batch* batch);
@@ -261,10 +264,11 @@ cacl_status cacl_batch_case(cacl_batch* batch, int i, cacl_ctx** out);
  * phi update, volume correction with a per-case lambda). */
 cacl_status cacl_batch_step(cacl_batch* batch, int nsteps);
 
-/* Launch shapes of the batched stages: collide-stream rows of 64, 128 or
- * 256 threads with a resident-sized grid striding through the work-list
- * (lb_variant 0, 1, 2) or one block per row (3, 4, 5), and the phi-update
- * tile (0..3, as CACL_OPT_PHASE_TILE). */
+/* Launch shapes of the batched stages: collide-stream blocks of 64, 128 or
+ * 256 threads (each thread one, two or four consecutive nodes of a case, as
+ * the case would run alone) with a resident-sized grid striding through the
+ * work-list (lb_variant 0, 1, 2) or one block per work item (3, 4, 5), and
+ * the phi-update tile (0..3, as CACL_OPT_PHASE_TILE). */
 cacl_status cacl_batch_set_option(cacl_batch* batch, int lb_variant,
                                   int phase_variant);
 
@@ -278,11 +282,15 @@ cacl_status cacl_batch_autotune(cacl_batch* batch, int steps, int* lb_variant,
  * order). CACL_OPT_PHASE_TILE selects the tile of the phase update:
  * 0 = 32x16 nodes x 16 planes, 1 = 32x8 x 16, 2 = 32x8 x 32,
  * 3 = 32x16 x 32. CACL_OPT_PHASE_PIPE selects how the phase update stages
- * its planes in shared memory: 0 = automatic (asynchronous 16-byte copies
- * when nx is a multiple of 4 and the fields are 16-byte aligned, else
- * staging through registers), 1 = registers, 2 = asynchronous copies
- * (CACL_ERR_ARG when nx is not a multiple of 4 or nz < 2). Both give
- * bit-identical results. CACL_OPT_LB_PIPE selects how the collide-stream
+ * its planes in shared memory and how many nodes a thread evaluates:
+ * 0 = automatic (3 when nx is a multiple of 4, nz >= 2 and the fields are
+ * 16-byte aligned, else 1), 1 = staging through registers, 2 = asynchronous
+ * 16-byte copies, two nodes per thread along y, 3 = asynchronous copies,
+ * 2 x 2 nodes per thread (an x pair on two rows, packed pair arithmetic);
+ * 2 and 3 return CACL_ERR_ARG when nx is not a multiple of 4 or nz < 2. All
+ * give bit-identical phi*; the partial sums of the volume correction agree
+ * to the rounding of their summation order, bit for bit between 1 and 2.
+ * CACL_OPT_LB_PIPE selects how the collide-stream
  * reads its 27 pulled population rows and 9 phi rows: 0 = direct loads
  * through the cache with two x-adjacent nodes per thread, one aligned
  * access per pair and packed pair arithmetic (the default; when nx is odd

@@ -36,7 +36,7 @@ EXPORTS = (
     "cacl_slab_halo", "cacl_slab_halo_bytes",
 )
 OPT_PHASE_TILE = 1
-OPT_PHASE_PIPE = 2  # 0 auto, 1 register staging, 2 asynchronous copies
+OPT_PHASE_PIPE = 2  # 0 auto, 1 registers, 2 copies (2 nodes/thread), 3 copies (2 x 2)
 OPT_LB_PIPE = 3  # 0 direct loads, 1 bulk-copy staged rows
 
 

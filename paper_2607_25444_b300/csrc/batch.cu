@@ -1,7 +1,9 @@
 // batch.cu -- many CAC-LB cases of uneven size advanced together: every
-// stage of the step is one grid-strided launch over a work-list that spans
-// all cases, the step is captured in a CUDA graph, and an autotuner picks
-// the collide-stream row length and the phi-update tile.
+// stage of the step is a grid-strided launch over a work-list that spans
+// all cases of one kernel shape (the collide-stream one launch per node
+// width, the phi update one per staging pipeline, as each case would run
+// alone), the step is captured in a CUDA graph, and an autotuner picks the
+// collide-stream block size and the phi-update tile.
 //
 // Each case keeps its own context (cacl_ctx) for set-up, queries and its
 // device buffers; the batch holds a device table of per-case descriptors and
@@ -21,11 +23,16 @@ struct cacl_batch {
   int lb_variant = 1;
   int phase_variant = 2;
   CaseDesc* d_cases = nullptr;
-  int* d_starts = nullptr;  // five lists of ncases + 1 starts
-  // phi update: cases staged through registers (wl_phase) and cases that
-  // qualify for copy staging (wl_phase_copy), as each would run alone
-  WorkList wl_lb{}, wl_phase{}, wl_phase_copy{}, wl_ghost{}, wl_corr{};
-  int grid_lb = 0, grid_phase = 0, grid_phase_copy = 0, grid_ghost = 0, grid_corr = 0;
+  int* d_starts = nullptr;  // NLISTS lists of ncases + 1 starts
+  // collide-stream: the cases of one, two and four nodes per thread
+  // (wl_lb[0..2]); phi update: cases staged through registers (wl_phase),
+  // by copies with two nodes per thread (wl_phase_copy) and with 2 x 2
+  // (wl_phase_quad); each as the case would run alone
+  WorkList wl_lb[3]{}, wl_phase{}, wl_phase_copy{}, wl_phase_quad{}, wl_ghost{},
+      wl_corr{};
+  int grid_lb[3] = {0, 0, 0};
+  int grid_phase = 0, grid_phase_copy = 0, grid_phase_quad = 0, grid_ghost = 0,
+      grid_corr = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool plan_ok = false;
   std::vector<int> geom_version;  // of each case when the plan was built
@@ -34,6 +41,9 @@ struct cacl_batch {
 };
 
 namespace {
+
+constexpr int NLISTS = 8;
+constexpr int LB_WIDTH[3] = {1, 2, 4};
 
 cacl_status bfail(cacl_batch* b, cacl_status st, const std::string& msg) {
   if (b) b->err = msg;
@@ -68,12 +78,13 @@ cacl_status build_plan(cacl_batch* b) {
   std::vector<CaseDesc> desc(nc);
   b->phase_nb.assign(nc, 0);
   b->geom_version.assign(nc, -1);
-  std::vector<int> starts(5 * (nc + 1), 0);
-  int* s_lb = starts.data();
-  int* s_ph = s_lb + (nc + 1);
+  std::vector<int> starts(NLISTS * (nc + 1), 0);
+  int* s_ph = starts.data();
   int* s_gh = s_ph + (nc + 1);
   int* s_cr = s_gh + (nc + 1);
   int* s_pc = s_cr + (nc + 1);
+  int* s_lb[3] = {s_pc + (nc + 1), s_pc + 2 * (nc + 1), s_pc + 3 * (nc + 1)};
+  int* s_pq = s_pc + 4 * (nc + 1);
   const int row = lb_batch_row(b->lb_variant);
   int ty = 16, zc = 16;
   phase_tile(b->phase_variant, ty, zc);
@@ -105,11 +116,25 @@ cacl_status build_plan(cacl_batch* b) {
     b->geom_version[i] = c->geom_version;
     if (d.phase_nb > c->part_blocks)
       return bfail(b, CACL_ERR_STATE, "partial-sum storage too small");
-    s_lb[i + 1] = s_lb[i] + ((c->g.nx + row - 1) / row) * c->g.ny * c->g.nz;
+    // nodes per thread of the collide-stream: the kernel the case gets alone
+    // (four-node for 16-bit populations, two-node, one-node), for both
+    // population buffers and both phi buffers
+    const bool quad = lb_quad_ok(c, c->f[0], c->f[1], c->phi[0]) &&
+                      lb_quad_ok(c, c->f[1], c->f[0], c->phi[1]);
+    const bool pair = lb_pair_ok(c, c->f[0], c->f[1], c->phi[0]) &&
+                      lb_pair_ok(c, c->f[1], c->f[0], c->phi[1]);
+    d.lbw = quad ? 4 : (pair ? 2 : 1);
+    const int wc = quad ? 2 : (pair ? 1 : 0);
+    for (int w = 0; w < 3; ++w) {
+      const int64_t units = c->g.N / d.lbw;
+      s_lb[w][i + 1] = s_lb[w][i] + (w == wc ? (int)((units + row - 1) / row) : 0);
+    }
     const bool copy = c->phase_pipe != 1 &&
                       phase_copy_ok(c->g, c->phi[0], c->phi[1], c->a, c->u, c->flags);
+    const bool two = copy && c->phase_pipe == 2;  // else 2 x 2
     s_ph[i + 1] = s_ph[i] + (copy ? 0 : d.phase_nb);
-    s_pc[i + 1] = s_pc[i] + (copy ? d.phase_nb : 0);
+    s_pc[i + 1] = s_pc[i] + (two ? d.phase_nb : 0);
+    s_pq[i + 1] = s_pq[i] + (copy && !two ? d.phase_nb : 0);
     s_gh[i + 1] = s_gh[i] + (c->wall_count + ghost_batch_block() - 1) /
                                 ghost_batch_block();
     const int64_t per = correct_batch_nodes();
@@ -120,23 +145,32 @@ cacl_status build_plan(cacl_batch* b) {
   BCK(cudaMemcpyAsync(b->d_starts, starts.data(), sizeof(int) * starts.size(),
                       cudaMemcpyHostToDevice, b->stream), "upload work-lists");
   BCK(cudaStreamSynchronize(b->stream), "sync");
-  b->wl_lb = {b->d_starts, nc, s_lb[nc]};
-  b->wl_phase = {b->d_starts + (nc + 1), nc, s_ph[nc]};
-  b->wl_ghost = {b->d_starts + 2 * (nc + 1), nc, s_gh[nc]};
-  b->wl_corr = {b->d_starts + 3 * (nc + 1), nc, s_cr[nc]};
-  b->wl_phase_copy = {b->d_starts + 4 * (nc + 1), nc, s_pc[nc]};
+  b->wl_phase = {b->d_starts, nc, s_ph[nc]};
+  b->wl_ghost = {b->d_starts + (nc + 1), nc, s_gh[nc]};
+  b->wl_corr = {b->d_starts + 2 * (nc + 1), nc, s_cr[nc]};
+  b->wl_phase_copy = {b->d_starts + 3 * (nc + 1), nc, s_pc[nc]};
+  for (int w = 0; w < 3; ++w)
+    b->wl_lb[w] = {b->d_starts + (4 + w) * (nc + 1), nc, s_lb[w][nc]};
+  b->wl_phase_quad = {b->d_starts + 7 * (nc + 1), nc, s_pq[nc]};
   // persistent grids: as many blocks as stay resident, at most the work
   const int sms = sm_count();
   auto grid_for = [&](int total, int per_sm) {
     const int cap = sms * (per_sm > 0 ? per_sm : 1);
     return total < cap ? (total > 0 ? total : 1) : cap;
   };
-  b->grid_lb = lb_batch_persistent(b->lb_variant)
-                   ? grid_for(b->wl_lb.total, lb_batch_occupancy(b->storage, b->lb_variant))
-                   : b->wl_lb.total;
+  for (int w = 0; w < 3; ++w)
+    b->grid_lb[w] =
+        b->wl_lb[w].total == 0
+            ? 0
+            : (lb_batch_persistent(b->lb_variant)
+                   ? grid_for(b->wl_lb[w].total,
+                              lb_batch_occupancy(b->storage, LB_WIDTH[w], b->lb_variant))
+                   : b->wl_lb[w].total);
   b->grid_phase = grid_for(b->wl_phase.total, phase_batch_occupancy(b->phase_variant));
   b->grid_phase_copy =
       grid_for(b->wl_phase_copy.total, phase_batch_copy_occupancy(b->phase_variant));
+  b->grid_phase_quad =
+      grid_for(b->wl_phase_quad.total, phase_batch_quad_occupancy(b->phase_variant));
   b->grid_ghost = grid_for(b->wl_ghost.total, 8);
   b->grid_corr = grid_for(b->wl_corr.total, 8);
   b->plan_ok = true;
@@ -148,9 +182,12 @@ cudaError_t enqueue_batch_step(cacl_batch* b, int par) {
   if ((e = launch_ghost_batch(b->d_cases, b->wl_ghost, b->grid_ghost, par,
                               b->stream)) != cudaSuccess)
     return e;
-  if ((e = launch_lb_batch(b->d_cases, b->wl_lb, b->storage, b->lb_variant,
-                           b->grid_lb, par, par, b->stream)) != cudaSuccess)
-    return e;
+  for (int w = 0; w < 3; ++w)
+    if (b->wl_lb[w].total > 0 &&
+        (e = launch_lb_batch(b->d_cases, b->wl_lb[w], b->storage, LB_WIDTH[w],
+                             b->lb_variant, b->grid_lb[w], par, par, b->stream)) !=
+            cudaSuccess)
+      return e;
   if (b->wl_phase.total > 0 &&
       (e = launch_phase_batch(b->d_cases, b->wl_phase, b->phase_variant,
                               b->grid_phase, par, b->stream)) != cudaSuccess)
@@ -158,6 +195,10 @@ cudaError_t enqueue_batch_step(cacl_batch* b, int par) {
   if (b->wl_phase_copy.total > 0 &&
       (e = launch_phase_batch_copy(b->d_cases, b->wl_phase_copy, b->phase_variant,
                                    b->grid_phase_copy, par, b->stream)) != cudaSuccess)
+    return e;
+  if (b->wl_phase_quad.total > 0 &&
+      (e = launch_phase_batch_quad(b->d_cases, b->wl_phase_quad, b->phase_variant,
+                                   b->grid_phase_quad, par, b->stream)) != cudaSuccess)
     return e;
   return launch_correct_batch(b->d_cases, (int)b->cases.size(), b->wl_corr,
                               b->grid_corr, par, b->stream);
@@ -190,6 +231,10 @@ cacl_status cacl_batch_create(const cacl_params* params, int ncases,
   for (int i = 1; i < ncases; ++i)
     if (params[i].storage != params[0].storage) return CACL_ERR_ARG;
   if (params[0].storage == CACL_F32_MOMENTS) return CACL_ERR_ARG;  // population forms only
+  for (int i = 0; i < ncases; ++i) {  // the batched kernels index with 32 bits
+    const int64_t n = (int64_t)params[i].nx * params[i].ny * params[i].nz;
+    if (n > 0 && (int64_t)Q * n >= (int64_t)INT32_MAX) return CACL_ERR_TOO_LARGE;
+  }
   cacl_batch* b = new cacl_batch();
   b->storage = params[0].storage;
   if (stream) {
@@ -211,7 +256,7 @@ cacl_status cacl_batch_create(const cacl_params* params, int ncases,
     b->cases.push_back(c);
   }
   if (cudaMalloc(&b->d_cases, sizeof(CaseDesc) * ncases) != cudaSuccess ||
-      cudaMalloc(&b->d_starts, sizeof(int) * 5 * (ncases + 1)) != cudaSuccess) {
+      cudaMalloc(&b->d_starts, sizeof(int) * NLISTS * (ncases + 1)) != cudaSuccess) {
     cacl_batch_destroy(b);
     return CACL_ERR_CUDA;
   }

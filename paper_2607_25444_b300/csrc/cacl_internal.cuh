@@ -317,6 +317,7 @@ struct CaseDesc {
   double* partials;
   MassScalars* mass;
   int phase_nb;  // phase-update blocks of this case for the batch's tile
+  int lbw;       // nodes per thread of the batched collide-stream (1, 2, 4)
 };
 
 // Virtual block b of a work-list belongs to case c when
@@ -485,25 +486,30 @@ void adjoint_free(AdjointState* s);
 
 // Batched stages: one grid-strided launch runs the stage for every case of
 // a work-list; fc / pc select each case's current population / phi buffer.
-// collide-stream rows of 64, 128, 256 threads, persistent (variants 0-2)
-// or one block per row (3-5)
+// collide-stream blocks of 64, 128, 256 threads, persistent (variants 0-2)
+// or one block per work item (3-5); one launch per node width (1, 2, 4
+// nodes per thread) over the cases of that width
 constexpr int LB_BATCH_VARIANTS = 6;
 int lb_batch_row(int variant);
 bool lb_batch_persistent(int variant);
-cudaError_t launch_lb_batch(const CaseDesc* cases, WorkList wl, int storage,
+cudaError_t launch_lb_batch(const CaseDesc* cases, WorkList wl, int storage, int width,
                             int variant, int grid, int fc, int pc,
                             cudaStream_t st);
-int lb_batch_occupancy(int storage, int variant);
+int lb_batch_occupancy(int storage, int width, int variant);
 cudaError_t launch_ghost_batch(const CaseDesc* cases, WorkList wl, int grid,
                                int pc, cudaStream_t st);
 int ghost_batch_block();
 cudaError_t launch_phase_batch(const CaseDesc* cases, WorkList wl, int variant,
                                int grid, int pc, cudaStream_t st);
 int phase_batch_occupancy(int variant);
-// the same over cases that qualify for copy staging (phase_copy_ok)
+// the same over cases that qualify for copy staging (phase_copy_ok): two
+// nodes per thread along y (phase pipeline 2) or 2 x 2 (0 and 3)
 cudaError_t launch_phase_batch_copy(const CaseDesc* cases, WorkList wl, int variant,
                                     int grid, int pc, cudaStream_t st);
 int phase_batch_copy_occupancy(int variant);
+cudaError_t launch_phase_batch_quad(const CaseDesc* cases, WorkList wl, int variant,
+                                    int grid, int pc, cudaStream_t st);
+int phase_batch_quad_occupancy(int variant);
 bool phase_copy_ok(const Grid& g, const void* phi_in, const void* phi_out,
                    const void* a, const void* u, const void* flags);
 void phase_tile(int variant, int& ty, int& zc);

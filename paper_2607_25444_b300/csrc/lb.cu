@@ -1456,15 +1456,30 @@ moments_init(float* __restrict__ C0, float* __restrict__ C1, float* __restrict__
   store_coefs(C1, n, N, c);
 }
 
-// Batched collide-stream: virtual block b of the work-list is row block
-// (bx, y, z) of its case; rows of BX threads along x. Blocks stride through
-// the work-list (b, b + gridDim.x, ...) so that the rows in flight at any
-// time are neighbours, as in a plain launch, and their phi stencils share
-// cache lines; the case changes every few thousand rows.
+// Batched collide-stream, W nodes per thread. The cases of the work-list
+// are those that run the W-node kernel alone (four-node for 16-bit
+// populations with nx a multiple of 4, two-node with nx even, else
+// one-node). Their nodes are taken in linear order n = x + nx (y + ny z) in
+// units of W nodes, and virtual block b of the work-list is the run of BX
+// units (b - start) BX .. of its case, so that only the last block of a
+// case has idle threads, whatever nx is. A unit of two or four nodes with a
+// solid node or a wall neighbour runs the one-node path on each node, as in
+// the single-case kernels: every node gets lb_node's arithmetic, bit for
+// bit. Blocks stride through the work-list (b, b + gridDim.x, ...), so that
+// the rows in flight at any time are neighbours and their phi stencils
+// share cache lines.
 // PERSIST: a resident-sized grid strides through the work-list; otherwise
 // one block per work item (the block scheduler does the distribution).
-template <typename Store, int BX, bool PERSIST>
-__global__ void __launch_bounds__(BX)
+// Registers: at most 168 for four nodes (three blocks of 128 threads per
+// SM; at 128 the case cursor and the linear indexing push the four-node
+// body into 300 bytes of spills), 96 for two (five blocks of 128).
+template <int W, int BX>
+constexpr int lb_batch_minb() {
+  return W == 4 ? (384 + BX - 1) / BX : (W == 2 ? 640 / BX : 1);
+}
+
+template <typename Store, int W, int BX, bool PERSIST>
+__global__ void __launch_bounds__(BX, (lb_batch_minb<W, BX>()))
 lb_collide_batch(const CaseDesc* __restrict__ cases, WorkList wl, int fc,
                  int pc) {
   using T = typename Store::T;
@@ -1475,15 +1490,32 @@ lb_collide_batch(const CaseDesc* __restrict__ cases, WorkList wl, int fc,
   for (int b = blockIdx.x; b < wl.total; b += stride) {
     cur.seek(cases, wl, b);
     const CaseDesc& cd = cur.d;
-    const int nbx = (cd.g.nx + BX - 1) / BX;
-    const int local = b - cur.cstart;
-    const int bx = local % nbx;
-    const int row = local / nbx;
-    const int y = row % cd.g.ny, z = row / cd.g.ny;
-    const int x = bx * BX + threadIdx.x;
-    if (x < cd.g.nx)
-      lb_node<Store, int>(x, y, z, (const T*)cd.f[fc], (T*)cd.f[1 - fc],
-                          cd.phi[pc], cd.u, cd.a, cd.flags, cd.g, cd.k);
+    const int n = ((b - cur.cstart) * BX + (int)threadIdx.x) * W;
+    if (n >= (int)cd.g.N) continue;
+    const int nxy = cd.g.nx * cd.g.ny;
+    const int z = n / nxy;
+    const int r = n - z * nxy;
+    const int y = r / cd.g.nx;
+    const int x0 = r - y * cd.g.nx;
+    const T* fin = (const T*)cd.f[fc];
+    T* fout = (T*)cd.f[1 - fc];
+    const float* phi = cd.phi[pc];
+    bool bulk = false;
+    if constexpr (W == 4 && sizeof(T) == 2) {
+      const uchar4 fl = *reinterpret_cast<const uchar4*>(cd.flags + n);
+      bulk = ((fl.x | fl.y | fl.z | fl.w) & (FLAG_SOLID | FLAG_NEAR)) == 0;
+      if (bulk) lb_quad<Store>(x0, y, z, fin, fout, phi, cd.u, cd.a, cd.g, cd.k);
+    } else if constexpr (W == 2) {
+      const uchar2 fl = *reinterpret_cast<const uchar2*>(cd.flags + n);
+      bulk = ((fl.x | fl.y) & (FLAG_SOLID | FLAG_NEAR)) == 0;
+      if (bulk) lb_pair<Store>(x0, y, z, fin, fout, phi, cd.u, cd.a, cd.g, cd.k);
+    }
+    if (!bulk) {
+#pragma unroll 1
+      for (int j = 0; j < W; ++j)
+        lb_node<Store, int>(x0 + j, y, z, fin, fout, phi, cd.u, cd.a, cd.flags, cd.g,
+                            cd.k);
+    }
   }
 }
 
@@ -1751,37 +1783,45 @@ int lb_batch_row(int variant) {
 bool lb_batch_persistent(int variant) { return variant < 3; }
 
 namespace {
-template <typename Store>
+template <typename Store, int W>
 void* lb_batch_fn(int variant) {
   switch (variant) {
-    case 0: return (void*)lb_collide_batch<Store, 64, true>;
-    case 2: return (void*)lb_collide_batch<Store, 256, true>;
-    case 3: return (void*)lb_collide_batch<Store, 64, false>;
-    case 4: return (void*)lb_collide_batch<Store, 128, false>;
-    case 5: return (void*)lb_collide_batch<Store, 256, false>;
-    default: return (void*)lb_collide_batch<Store, 128, true>;
+    case 0: return (void*)lb_collide_batch<Store, W, 64, true>;
+    case 2: return (void*)lb_collide_batch<Store, W, 256, true>;
+    case 3: return (void*)lb_collide_batch<Store, W, 64, false>;
+    case 4: return (void*)lb_collide_batch<Store, W, 128, false>;
+    case 5: return (void*)lb_collide_batch<Store, W, 256, false>;
+    default: return (void*)lb_collide_batch<Store, W, 128, true>;
   }
 }
 
-void* lb_batch_kernel(int storage, int variant) {
+template <typename Store>
+void* lb_batch_width(int width, int variant) {
+  if constexpr (sizeof(typename Store::T) == 2) {
+    if (width == 4) return lb_batch_fn<Store, 4>(variant);
+  }
+  return width == 2 ? lb_batch_fn<Store, 2>(variant) : lb_batch_fn<Store, 1>(variant);
+}
+
+void* lb_batch_kernel(int storage, int width, int variant) {
   switch (storage) {
-    case CACL_F16_SHIFTED: return lb_batch_fn<StoreF16>(variant);
-    case CACL_BF16_SHIFTED: return lb_batch_fn<StoreBF16>(variant);
-    default: return lb_batch_fn<StoreF32>(variant);
+    case CACL_F16_SHIFTED: return lb_batch_width<StoreF16>(width, variant);
+    case CACL_BF16_SHIFTED: return lb_batch_width<StoreBF16>(width, variant);
+    default: return lb_batch_width<StoreF32>(width == 4 ? 1 : width, variant);
   }
 }
 }  // namespace
 
-int lb_batch_occupancy(int storage, int variant) {
+int lb_batch_occupancy(int storage, int width, int variant) {
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lb_batch_kernel(storage, variant),
-                                                lb_batch_row(variant), 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &nb, lb_batch_kernel(storage, width, variant), lb_batch_row(variant), 0);
   return nb;
 }
 
-cudaError_t launch_lb_batch(const CaseDesc* cases, WorkList wl, int storage,
+cudaError_t launch_lb_batch(const CaseDesc* cases, WorkList wl, int storage, int width,
                             int variant, int grid, int fc, int pc, cudaStream_t st) {
-  void* fn = lb_batch_kernel(storage, variant);
+  void* fn = lb_batch_kernel(storage, width, variant);
   void* args[] = {(void*)&cases, (void*)&wl, (void*)&fc, (void*)&pc};
   return cudaLaunchKernel(fn, dim3(grid), dim3(lb_batch_row(variant)), args, 0, st);
 }

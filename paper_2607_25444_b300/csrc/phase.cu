@@ -24,6 +24,8 @@
 // Partial sums are accumulated per thread as unevaluated float pairs
 // (Knuth's two-sum), combined across the block the same way, and written as
 // FP64 per block: FP64 arithmetic stays out of the per-node path.
+#include <type_traits>
+
 #include "cacl_internal.cuh"
 
 namespace cacl {
@@ -54,6 +56,22 @@ __device__ __forceinline__ DF df_merge(DF a, DF b) {
   return r;
 }
 
+// two independent compensated sums, one per lane of an x pair, advanced in
+// packed pair operations (each lane as df_add)
+struct DF2 {
+  float2 hi, lo;
+};
+
+__device__ __forceinline__ void df2_add(DF2& s, float2 x) {
+  const float2 t = vadd(s.hi, x);
+  const float2 bb = vsub(t, s.hi);
+  const float2 err = vadd(vsub(s.hi, vsub(t, bb)), vsub(x, bb));
+  s.hi = t;
+  s.lo = vadd(s.lo, err);
+}
+__device__ __forceinline__ DF lane_x(const DF2& s) { return {s.hi.x, s.lo.x}; }
+__device__ __forceinline__ DF lane_y(const DF2& s) { return {s.hi.y, s.lo.y}; }
+
 __device__ __forceinline__ DF df_shfl_down(DF v, int off) {
   DF r;
   r.hi = __shfl_down_sync(0xffffffffu, v.hi, off);
@@ -62,10 +80,32 @@ __device__ __forceinline__ DF df_shfl_down(DF v, int off) {
 }
 
 // minmod(a, b) = 0 if a b <= 0, else sign(a) min(|a|, |b|) (Eq. minmod),
-// evaluated as max(min(a, b), min(max(a, b), 0)): for a, b > 0 it gives
-// min(a, b), for a, b < 0 max(a, b), and 0 for opposite signs or a zero.
+// which is the median of a, b and 0, evaluated as
+// max(min(a, b), min(a, 0), min(b, 0)): for a, b > 0 it gives min(a, b),
+// for a, b < 0 max(a, b), and 0 for opposite signs or a zero. min(d, 0) of
+// a difference can serve both slopes next to it (minmod_m). Every step is
+// exact, so any evaluation order gives the same bits.
+__device__ __forceinline__ float max3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float neg_part(float d) { return fminf(d, 0.f); }
+// minmod from the differences and their neg_part
+__device__ __forceinline__ float minmod_m(float a, float b, float ma, float mb) {
+  return max3(fminf(a, b), ma, mb);
+}
 __device__ __forceinline__ float minmod(float a, float b) {
-  return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.f));
+  return minmod_m(a, b, neg_part(a), neg_part(b));
+}
+__device__ __forceinline__ float2 minmod(float2 a, float2 b) {
+  return make_float2(minmod(a.x, b.x), minmod(a.y, b.y));
+}
+__device__ __forceinline__ float2 neg_part(float2 d) {
+  return make_float2(neg_part(d.x), neg_part(d.y));
+}
+__device__ __forceinline__ float2 minmod_m(float2 a, float2 b, float2 ma, float2 mb) {
+  return make_float2(minmod_m(a.x, b.x, ma.x, mb.x), minmod_m(a.y, b.y, ma.y, mb.y));
 }
 
 __device__ __forceinline__ int mod(int i, int n) {
@@ -78,14 +118,65 @@ __device__ __forceinline__ int wrap1(int i, int n) {
   return i < 0 ? i + n : (i >= n ? i - n : i);
 }
 
+// The arithmetic of a node, shared by every phi-update kernel. Each
+// operation rounds once, in the order written (vfma, vmul, vadd, vsub leave
+// no contraction to the compiler), so kernels that evaluate one node or a
+// packed pair of nodes at a time give the same bits at every node.
+
+// upwind state: pl where uf >= 0, else pr (per lane)
+__device__ __forceinline__ float upwind(float uf, float pl, float pr) {
+  return uf >= 0.f ? pl : pr;
+}
+__device__ __forceinline__ float2 upwind(float2 uf, float2 pl, float2 pr) {
+  return make_float2(uf.x >= 0.f ? pl.x : pr.x, uf.y >= 0.f ? pl.y : pr.y);
+}
+
 // Upwind flux u_f phi_f through the face between cells l and r (Eqs.
 // face_flux_def, recon_lr_x, upwind_select_x): u_f = (u_l + u_r) / 2, and
 // phi_f the left state phi_l + s_l / 2 when u_f >= 0, else the right state
 // phi_r - s_r / 2 (s the minmod slopes).
-__device__ __forceinline__ float face_flux(float ul, float ur, float vl,
-                                           float sl, float vr, float sr) {
-  const float uf = 0.5f * (ul + ur);
-  return uf * ((uf >= 0.f) ? fmaf(0.5f, sl, vl) : fmaf(-0.5f, sr, vr));
+template <typename V>
+__device__ __forceinline__ V face_flux(V ul, V ur, V vl, V sl, V vr, V sr) {
+  const V uf = vmul(splat<V>(0.5f), vadd(ul, ur));
+  return vmul(uf, upwind(uf, vfma(splat<V>(0.5f), sl, vl), vfma(splat<V>(-0.5f), sr, vr)));
+}
+
+// a + 4 b + c, the three-point sum of the factored D3Q27 weights (times 6)
+template <typename V>
+__device__ __forceinline__ V sum141(V a, V b, V c) {
+  return vadd(a, vfma(splat<V>(4.f), b, c));
+}
+
+// In-plane partial stencils of one output node (times 36 undone):
+// H = Dd_x S_y a_x + S_x Dd_y a_y from S_y a_x at x + 1 and x - 1 and Dd_y
+// a_y (times 6) at x - 1, x, x + 1; V or L = S_y of the S_x row sums.
+template <typename V>
+__device__ __forceinline__ V partial_h(V sxp, V sxm, V d0, V d1, V d2) {
+  return vmul(splat<V>(1.0f / 36.0f),
+              vadd(vadd(vsub(sxp, sxm), d0), vfma(splat<V>(4.f), d1, d2)));
+}
+template <typename V>
+__device__ __forceinline__ V partial_s(V r0, V r1, V r2) {
+  return vmul(splat<V>(1.0f / 36.0f), sum141(r0, r1, r2));
+}
+
+// Eq. phi_update_muscl with the isotropic diffusion and the compressive
+// term: phi* = phi - div F + D lap phi - kappa div_iso a, with
+// lap = 6 (S_z L - phi) and div_iso a = 3 S_z H + 3 Dd_z V written through
+// the carried partials of planes kz-1 .. kz+1.
+template <typename V>
+__device__ __forceinline__ V node_update(V v0, V div, V l0, V l1, V l2, V h0, V h1,
+                                         V h2, V vv0, V vv2, const Consts& k) {
+  const V lap = vfma(splat<V>(-6.f), v0, sum141(l0, l1, l2));
+  const V diva = vmul(splat<V>(0.5f), vsub(vadd(sum141(h0, h1, h2), vv2), vv0));
+  return vfma(splat<V>(-k.kappa), diva, vfma(splat<V>(k.mobility), lap, vsub(v0, div)));
+}
+
+// chi(phi*) = phi* (1 - phi*) inside the band eps < phi* < 1 - eps (Eq.
+// mass_correction_normalization), else 0
+__device__ __forceinline__ float band_chi(float vs, const Consts& k) {
+  return (vs > k.eps_phi && vs < 1.0f - k.eps_phi) ? __fmul_rn(vs, __fadd_rn(1.0f, -vs))
+                                                     : 0.f;
 }
 
 // Net advective flux difference along one axis (Eqs. divF .. upwind_select):
@@ -95,12 +186,12 @@ __device__ __forceinline__ float muscl_axis(float vm2, float vm1, float v0,
                                             float vp1, float vp2, bool solm,
                                             bool solp, float um, float uc,
                                             float up) {
-  const float sm = minmod(vm1 - vm2, v0 - vm1);
-  const float s0 = minmod(v0 - vm1, vp1 - v0);
-  const float sp = minmod(vp1 - v0, vp2 - vp1);
+  const float sm = minmod(vsub(vm1, vm2), vsub(v0, vm1));
+  const float s0 = minmod(vsub(v0, vm1), vsub(vp1, v0));
+  const float sp = minmod(vsub(vp1, v0), vsub(vp2, vp1));
   const float fp = face_flux(uc, up, v0, s0, vp1, sp);
   const float fm = face_flux(um, uc, vm1, sm, v0, s0);
-  return (solp ? 0.f : fp) - (solm ? 0.f : fm);
+  return vsub(solp ? 0.f : fp, solm ? 0.f : fm);
 }
 
 // Registers a thread carries up its pair of columns (output rows a and b)
@@ -161,20 +252,20 @@ __device__ __forceinline__ void march_roll(March& m, const float* P1,
   float H2[2], V2[2], L2[2];
 #pragma unroll
   for (int j = 0; j < 2; ++j) {  // output row j uses rows j .. j+2
-    const float sxp = xp_[j] + fmaf(4.f, xp_[j + 1], xp_[j + 2]);
-    const float sxm = xm_[j] + fmaf(4.f, xm_[j + 1], xm_[j + 2]);
-    const float d0 = ym_[j + 2][0] - ym_[j][0];
-    const float d1 = ym_[j + 2][1] - ym_[j][1];
-    const float d2 = ym_[j + 2][2] - ym_[j][2];
-    H2[j] = (sxp - sxm + d0 + fmaf(4.f, d1, d2)) * (1.0f / 36.0f);
+    const float sxp = sum141(xp_[j], xp_[j + 1], xp_[j + 2]);
+    const float sxm = sum141(xm_[j], xm_[j + 1], xm_[j + 2]);
+    const float d0 = vsub(ym_[j + 2][0], ym_[j][0]);
+    const float d1 = vsub(ym_[j + 2][1], ym_[j][1]);
+    const float d2 = vsub(ym_[j + 2][2], ym_[j][2]);
+    H2[j] = partial_h(sxp, sxm, d0, d1, d2);
     float rz[3], rl[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      rz[r] = zz[j + r][0] + fmaf(4.f, zz[j + r][1], zz[j + r][2]);
-      rl[r] = pp[j + r][0] + fmaf(4.f, pp[j + r][1], pp[j + r][2]);
+      rz[r] = sum141(zz[j + r][0], zz[j + r][1], zz[j + r][2]);
+      rl[r] = sum141(pp[j + r][0], pp[j + r][1], pp[j + r][2]);
     }
-    V2[j] = (rz[0] + fmaf(4.f, rz[1], rz[2])) * (1.0f / 36.0f);
-    L2[j] = (rl[0] + fmaf(4.f, rl[1], rl[2])) * (1.0f / 36.0f);
+    V2[j] = partial_s(rz[0], rz[1], rz[2]);
+    L2[j] = partial_s(rl[0], rl[1], rl[2]);
   }
   m.Ha[0] = m.Ha[1]; m.Ha[1] = m.Ha[2]; m.Ha[2] = H2[0];
   m.Hb[0] = m.Hb[1]; m.Hb[1] = m.Hb[2]; m.Hb[2] = H2[1];
@@ -187,8 +278,8 @@ __device__ __forceinline__ void march_roll(March& m, const float* P1,
   m.sa3[0] = m.sa3[1]; m.sa3[1] = m.sa3[2]; m.sa3[2] = (S1[cp] & FLAG_SOLID) != 0;
   m.sb3[0] = m.sb3[1]; m.sb3[1] = m.sb3[2]; m.sb3[2] = (S1[cp + PP] & FLAG_SOLID) != 0;
   // z slope at kz + 1 and z flux at kz + 1/2, from the slope at kz
-  const float sa1 = minmod(m.ca[1] - m.ca[0], m.ca[2] - m.ca[1]);
-  const float sb1 = minmod(m.cb[1] - m.cb[0], m.cb[2] - m.cb[1]);
+  const float sa1 = minmod(vsub(m.ca[1], m.ca[0]), vsub(m.ca[2], m.ca[1]));
+  const float sb1 = minmod(vsub(m.cb[1], m.cb[0]), vsub(m.cb[2], m.cb[1]));
   m.fzma = m.fzpa;
   m.fzmb = m.fzpb;
   m.fzpa = face_flux(m.uza[0], m.uza[1], m.ca[0], m.sza, m.ca[1], sa1);
@@ -212,19 +303,14 @@ __device__ __forceinline__ void march_node(
     *out = v0;
     return;
   }
-  float div = muscl_axis(P0[c - 2], P0[c - 1], v0, P0[c + 1], P0[c + 2],
-                         (S0[c - 1] & FLAG_SOLID) != 0,
-                         (S0[c + 1] & FLAG_SOLID) != 0, ux0, ux1, ux2);
-  div += dy;
-  div += dz;
-  // lap = 6 (S_z L - phi), div_iso a = 3 S_z H + 3 Dd_z V
-  const float lap = l0 + fmaf(4.f, l1, l2) - 6.f * v0;
-  const float diva = 0.5f * (h0 + fmaf(4.f, h1, h2) + vv2 - vv0);
-  const float vs = v0 - div + k.mobility * lap - k.kappa * diva;
+  const float dx = muscl_axis(P0[c - 2], P0[c - 1], v0, P0[c + 1], P0[c + 2],
+                              (S0[c - 1] & FLAG_SOLID) != 0,
+                              (S0[c + 1] & FLAG_SOLID) != 0, ux0, ux1, ux2);
+  const float vs = node_update(v0, vadd(vadd(dx, dy), dz), l0, l1, l2, h0, h1, h2,
+                               vv0, vv2, k);
   *out = vs;
   df_add(msum, vs);
-  const float chi = (vs > k.eps_phi && vs < 1.0f - k.eps_phi) ? vs * (1.0f - vs) : 0.f;
-  df_add(wsum, chi);
+  df_add(wsum, band_chi(vs, k));
 }
 
 // Both output nodes of the pair at plane kz: P0 / S0 hold phi and the flags
@@ -246,23 +332,23 @@ __device__ __forceinline__ void march_emit(March& m, const float* P0,
   const float va = m.ca[0], vb = m.cb[0];
   const bool sy0 = (S0[cp - PP] & FLAG_SOLID) != 0;
   const bool sy3 = (S0[cp + 2 * PP] & FLAG_SOLID) != 0;
-  const float s_m = minmod(py1 - py0, va - py1);  // y slopes at ya-1 .. yb+1
-  const float s_a = minmod(va - py1, vb - va);
-  const float s_b = minmod(vb - va, py4 - vb);
-  const float s_p = minmod(py4 - vb, py5 - py4);
+  const float s_m = minmod(vsub(py1, py0), vsub(va, py1));  // y slopes at ya-1 .. yb+1
+  const float s_a = minmod(vsub(va, py1), vsub(vb, va));
+  const float s_b = minmod(vsub(vb, va), vsub(py4, vb));
+  const float s_p = minmod(vsub(py4, vb), vsub(py5, py4));
   const float fy_m = face_flux(uy4[0], uy4[1], py1, s_m, va, s_a);  // ya-1/2
   const float fy_c = face_flux(uy4[1], uy4[2], va, s_a, vb, s_b);   // ya+1/2
   const float fy_p = face_flux(uy4[2], uy4[3], vb, s_b, py4, s_p);  // yb+1/2
   if (act_a) {
-    const float dy = (m.sb3[1] ? 0.f : fy_c) - (sy0 ? 0.f : fy_m);
-    const float dz = (m.sa3[2] ? 0.f : m.fzpa) - (m.sa3[0] ? 0.f : m.fzma);
+    const float dy = vsub(m.sb3[1] ? 0.f : fy_c, sy0 ? 0.f : fy_m);
+    const float dz = vsub(m.sa3[2] ? 0.f : m.fzpa, m.sa3[0] ? 0.f : m.fzma);
     march_node(m.msum, m.wsum, P0, S0, cp, va, m.sa3[1], dy, dz, uxa[0], uxa[1],
                uxa[2], m.Ha[0], m.Ha[1], m.Ha[2], m.Va[0], m.Va[2], m.La[0],
                m.La[1], m.La[2], outa, k);
   }
   if (act_b) {
-    const float dy = (sy3 ? 0.f : fy_p) - (m.sa3[1] ? 0.f : fy_c);
-    const float dz = (m.sb3[2] ? 0.f : m.fzpb) - (m.sb3[0] ? 0.f : m.fzmb);
+    const float dy = vsub(sy3 ? 0.f : fy_p, m.sa3[1] ? 0.f : fy_c);
+    const float dz = vsub(m.sb3[2] ? 0.f : m.fzpb, m.sb3[0] ? 0.f : m.fzmb);
     march_node(m.msum, m.wsum, P0, S0, cp + PP, vb, m.sb3[1], dy, dz, uxb[0],
                uxb[1], uxb[2], m.Hb[0], m.Hb[1], m.Hb[2], m.Vb[0], m.Vb[2],
                m.Lb[0], m.Lb[1], m.Lb[2], outb, k);
@@ -694,6 +780,429 @@ __device__ __forceinline__ void phase_tile_copy(
   block_partials<THREADS>(m.msum, m.wsum, tid, partials, pb, nblocks);
 }
 
+// ---- Copy-staged tile with 2 x 2 nodes per thread --------------------------
+// The same tile (TX x TYN nodes of a plane, marching up ZC planes) and the
+// same per-node arithmetic as phase_tile_copy, with each thread owning an x
+// pair of nodes on each of two rows: (x, x + 1) x (ya, ya + 1), x even. The
+// x pair is evaluated in packed pair operations (one instruction for both
+// nodes, rounded per node as the scalar one), shared-memory reads of the
+// pair are 8-byte, the x faces between the pair and the stencil sums of the
+// pair share their operands, and the copy jobs (phi with its flags, a and
+// u, the same windows as phase_tile_copy) are addressed from offsets fixed
+// once per tile. Bit-identical to the other phi-update kernels at every
+// node; the per-thread order of the partial sums differs, so M* and W
+// agree to rounding of the sums.
+constexpr int QTX = TX / 2;  // thread columns
+
+template <int TYN, int D>
+struct QuadTile {
+  static constexpr int PR = TYN + 4, AR = TYN + 2;  // phi rows, a rows
+  // the copies of step b + D are issued before the barrier of step b, while
+  // a thread may still be at step b - 1: they must miss the phi slots of
+  // planes t-1 .. t+1 and the a slot of plane t that it reads
+  static constexpr int RP = 4 + D, RA = 2 + D;
+  static constexpr int PHI = PR * CW;  // floats per phi slot
+  static constexpr int AC = AR * CW;   // floats per a component
+  // u_x of plane t (rows y0 .., all CW columns), u_y of plane t (rows
+  // y0-1 .., columns x0 .. x0+31), u_z of plane t + 1 (rows y0 .., 32
+  // columns), after a of plane t + 1
+  static constexpr int UX = TYN * CW, UY = (TYN + 2) * TX, UZ = TYN * TX;
+  static constexpr int ASLOT = 3 * AC + UX + UY + UZ;
+  static constexpr int FLG = PR * CW;  // bytes per flags slot
+  static constexpr int NPJ = PR * NCH, NAJ = AR * NCH;  // copy jobs per plane
+  static constexpr int NXJ = TYN * NCH, NYJ = (TYN + 2) * (TX / 4), NZJ = TYN * (TX / 4);
+  static constexpr size_t bytes =
+      sizeof(float) * ((size_t)RP * PHI + (size_t)RA * ASLOT) + (size_t)RP * FLG;
+};
+
+// solid bit of node i (0: (x, ya), 1: (x+1, ya), 2: (x, yb), 3: (x+1, yb))
+// of carried plane p (0: kz-1, 1: kz, 2: kz+1)
+__device__ __forceinline__ bool qsolid(uint32_t bits, int p, int i) {
+  return (bits >> (4 * p + i)) & 1u;
+}
+// the two solid flags of an x pair from two flag bytes read as one 16-bit
+// word (low byte: x, high byte: x + 1)
+__device__ __forceinline__ uint32_t pair_bits(const uint8_t* s) {
+  static_assert(FLAG_SOLID == 1, "solid flag in bit 0");
+  const uint32_t w = *reinterpret_cast<const uint16_t*>(s);
+  return (w & 1u) | ((w >> 7) & 2u);
+}
+__device__ __forceinline__ bool lo_solid(const uint8_t* s) {
+  return (*reinterpret_cast<const uint16_t*>(s) & FLAG_SOLID) != 0;
+}
+__device__ __forceinline__ bool hi_solid(const uint8_t* s) {
+  return (*reinterpret_cast<const uint16_t*>(s) & (FLAG_SOLID << 8)) != 0;
+}
+__device__ __forceinline__ float2 masked(bool sx, bool sy, float2 f) {
+  return make_float2(sx ? 0.f : f.x, sy ? 0.f : f.y);
+}
+__device__ __forceinline__ float2 ld2(const float* p) {
+  return *reinterpret_cast<const float2*>(p);
+}
+
+// Registers a thread carries up its 2 x 2 columns (pairs A: row ya, B: row
+// yb), as March does for a pair of rows.
+struct QMarch {
+  float2 cA[3], cB[3];  // phi at kz .. kz+2
+  uint32_t sol;         // solid bits of planes kz-1 .. kz+1 (qsolid)
+  float2 HA[3], HB[3], VA[3], VB[3], LA[3], LB[3];
+  float2 uzA[2], uzB[2];  // u_z at kz, kz+1
+  float2 szA, szB;        // z slope at kz + 1
+  float2 fzmA, fzmB, fzpA, fzpB;
+  DF2 msum, wsum;  // per lane of the x pair
+};
+
+// In-plane partials of one output row pair from rows r .. r+2 of the four
+// columns x-1 .. x+2 (a_x, a_y, a_z, phi rows as read from shared memory).
+__device__ __forceinline__ void quad_row_partials(const float (&ax)[4][4],
+                                                  const float (&ay)[4][4],
+                                                  const float2 (&rz)[4],
+                                                  const float2 (&rl)[4], int r,
+                                                  float2& H, float2& V, float2& L) {
+  auto col = [](const float (&f)[4][4], int row, int c) {
+    return make_float2(f[row][c], f[row][c + 1]);
+  };
+  // S_y a_x at (x-1, x) and (x+1, x+2)
+  const float2 sxm = sum141(col(ax, r, 0), col(ax, r + 1, 0), col(ax, r + 2, 0));
+  const float2 sxp = sum141(col(ax, r, 2), col(ax, r + 1, 2), col(ax, r + 2, 2));
+  // Dd_y a_y (times 6) at (x-1, x), (x, x+1), (x+1, x+2)
+  const float2 d0 = vsub(col(ay, r + 2, 0), col(ay, r, 0));
+  const float2 d1 = vsub(col(ay, r + 2, 1), col(ay, r, 1));
+  const float2 d2 = vsub(col(ay, r + 2, 2), col(ay, r, 2));
+  H = partial_h(sxp, sxm, d0, d1, d2);
+  V = partial_s(rz[r], rz[r + 1], rz[r + 2]);
+  L = partial_s(rl[r], rl[r + 1], rl[r + 2]);
+}
+
+// Advance the carried registers by one plane (as march_roll): partials of
+// plane kz + 1 (phi slot P1, a slot components ax / ay / az, all with row
+// pitch CW; cp and ca index (x, ya) in the phi and a windows), own phi at
+// kz + 2 (P2), solid flags at kz + 1 (S1), then the z slope at kz + 1 and
+// the z flux at kz + 1/2 (m.uz* must hold u_z at kz and kz + 1).
+__device__ __forceinline__ void quad_roll(QMarch& m, const float* P1, const float* P2,
+                                          const uint8_t* S1, const float* axp,
+                                          const float* ayp, const float* azp, int cp,
+                                          int ca) {
+  float ax[4][4], ay[4][4];
+  float2 rz[4], rl[4];
+  // columns x-1 .. x+2 of a row from the aligned pairs at x-2, x, x+2
+  auto row4 = [](const float* p, float (&v)[4]) {
+    const float2 l = ld2(p - 2), c = ld2(p), r = ld2(p + 2);
+    v[0] = l.y;
+    v[1] = c.x;
+    v[2] = c.y;
+    v[3] = r.x;
+  };
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {  // rows ya-1 .. yb+1, columns x-1 .. x+2
+    const int o = ca + (r - 1) * CW;
+    const int op = cp + (r - 1) * CW;
+    float zz[4], pp[4];
+    row4(axp + o, ax[r]);
+    row4(ayp + o, ay[r]);
+    row4(azp + o, zz);
+    row4(P1 + op, pp);
+    // S_x of the row at (x, x+1)
+    rz[r] = sum141(make_float2(zz[0], zz[1]), make_float2(zz[1], zz[2]),
+                   make_float2(zz[2], zz[3]));
+    rl[r] = sum141(make_float2(pp[0], pp[1]), make_float2(pp[1], pp[2]),
+                   make_float2(pp[2], pp[3]));
+  }
+  float2 HA, VA, LA, HB, VB, LB;
+  quad_row_partials(ax, ay, rz, rl, 0, HA, VA, LA);
+  quad_row_partials(ax, ay, rz, rl, 1, HB, VB, LB);
+  m.HA[0] = m.HA[1]; m.HA[1] = m.HA[2]; m.HA[2] = HA;
+  m.HB[0] = m.HB[1]; m.HB[1] = m.HB[2]; m.HB[2] = HB;
+  m.VA[0] = m.VA[1]; m.VA[1] = m.VA[2]; m.VA[2] = VA;
+  m.VB[0] = m.VB[1]; m.VB[1] = m.VB[2]; m.VB[2] = VB;
+  m.LA[0] = m.LA[1]; m.LA[1] = m.LA[2]; m.LA[2] = LA;
+  m.LB[0] = m.LB[1]; m.LB[1] = m.LB[2]; m.LB[2] = LB;
+  m.cA[0] = m.cA[1]; m.cA[1] = m.cA[2]; m.cA[2] = ld2(P2 + cp);
+  m.cB[0] = m.cB[1]; m.cB[1] = m.cB[2]; m.cB[2] = ld2(P2 + cp + CW);
+  m.sol = (m.sol >> 4) | (pair_bits(S1 + cp) << 8) | (pair_bits(S1 + cp + CW) << 10);
+  const float2 sA1 = minmod(vsub(m.cA[1], m.cA[0]), vsub(m.cA[2], m.cA[1]));
+  const float2 sB1 = minmod(vsub(m.cB[1], m.cB[0]), vsub(m.cB[2], m.cB[1]));
+  m.fzmA = m.fzpA;
+  m.fzmB = m.fzpB;
+  m.fzpA = face_flux(m.uzA[0], m.uzA[1], m.cA[0], m.szA, m.cA[1], sA1);
+  m.fzpB = face_flux(m.uzB[0], m.uzB[1], m.cB[0], m.szB, m.cB[1], sB1);
+  m.szA = sA1;
+  m.szB = sB1;
+}
+
+// x faces of one row pair at plane kz: phi at x-2 .. x+3 (pm, pc, pp),
+// u_x at x-1 (um), (x, x+1) (uc), x+2 (up), solid flags at x-1 .. x+2;
+// returns the masked flux differences of nodes x and x + 1.
+__device__ __forceinline__ float2 quad_x_faces(float2 pm, float2 pc, float2 pp,
+                                               float um, float2 uc, float up,
+                                               bool sm1, bool s0, bool s1, bool s2) {
+  // differences at x-3/2 .. x+5/2
+  const float dm3 = vsub(pm.y, pm.x), dm1 = vsub(pc.x, pm.y), d1 = vsub(pc.y, pc.x),
+              d3 = vsub(pp.x, pc.y), d5 = vsub(pp.y, pp.x);
+  const float mm3 = neg_part(dm3), mm1 = neg_part(dm1), m1 = neg_part(d1),
+              m3 = neg_part(d3), m5 = neg_part(d5);
+  const float sxm = minmod_m(dm3, dm1, mm3, mm1), sx0 = minmod_m(dm1, d1, mm1, m1),
+              sx1 = minmod_m(d1, d3, m1, m3), sx2 = minmod_m(d3, d5, m3, m5);
+  // faces (x-1/2, x+1/2) and (x+1/2, x+3/2)
+  const float2 fl = face_flux(make_float2(um, uc.x), uc, make_float2(pm.y, pc.x),
+                              make_float2(sxm, sx0), pc, make_float2(sx0, sx1));
+  const float2 fr = face_flux(uc, make_float2(uc.y, up), pc, make_float2(sx0, sx1),
+                              make_float2(pc.y, pp.x), make_float2(sx1, sx2));
+  return vsub(masked(s1, s2, fr), masked(sm1, s0, fl));
+}
+
+// One output row pair: phi*, its store and its partial sums (as march_node
+// per node; a node outside the grid or solid adds an exact zero, which
+// leaves the compensated sums unchanged). act: the pair is inside the grid.
+__device__ __forceinline__ void quad_nodes(DF2& msum, DF2& wsum, float2 v0, float2 div,
+                                           const float2 (&L)[3], const float2 (&H)[3],
+                                           const float2 (&Vz)[3], bool solx, bool soly,
+                                           bool act, float* out, const Consts& k) {
+  const float2 vs = node_update(v0, div, L[0], L[1], L[2], H[0], H[1], H[2], Vz[0],
+                                Vz[2], k);
+  if (act)
+    *reinterpret_cast<float2*>(out) = make_float2(solx ? v0.x : vs.x, soly ? v0.y : vs.y);
+  const float2 v = make_float2((act && !solx) ? vs.x : 0.f, (act && !soly) ? vs.y : 0.f);
+  df2_add(msum, v);
+  df2_add(wsum, make_float2(band_chi(v.x, k), band_chi(v.y, k)));
+}
+
+// The tile (bxi, byi, bzi) of one grid, 2 x 2 nodes per thread, staged by
+// asynchronous copies issued D planes ahead. Requires nx % 4 == 0 (every
+// 16-byte chunk of a plane row is aligned and the x pairs never straddle
+// the wrap) and 16-byte aligned fields. smem: QuadTile<TYN, D>::bytes.
+// Ring slots and plane offsets advance by one per step (no division); the
+// first two steps, which only fill the carried registers, are peeled.
+template <int TYN, int ZC, int D>
+__device__ __forceinline__ void phase_tile_quad(
+    int bxi, int byi, int bzi, int pb, const float* __restrict__ phi,
+    const float* __restrict__ afld, float* __restrict__ phi_out,
+    const float* __restrict__ u, const uint8_t* __restrict__ flags,
+    double* __restrict__ partials, int nblocks, const Grid& g, const Consts& k,
+    float* smem, int zbase, int zlim) {
+  using L = QuadTile<TYN, D>;
+  constexpr int THREADS = QTX * TYN / 2;
+  static_assert(L::NPJ <= 2 * THREADS && L::NAJ <= 2 * THREADS && L::NXJ <= 2 * THREADS &&
+                    L::NYJ <= 2 * THREADS && L::NZJ <= THREADS,
+                "at most two copy jobs of a kind a thread");
+  float* s_phi = smem;                                   // [RP][PHI]
+  float* s_a = smem + L::RP * L::PHI;                    // [RA][3][AC]
+  uint8_t* s_flg = (uint8_t*)(s_a + L::RA * L::ASLOT);   // [RP][FLG]
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = tx + QTX * ty;
+  const int x0 = bxi * TX, y0 = byi * TYN, z0 = zbase + bzi * ZC;
+  const int zend = min(z0 + ZC, zlim);
+  const int nx = g.nx, ny = g.ny, nxy = nx * ny;
+  const int64_t N = g.N;
+  const int64_t nzxy = (int64_t)g.nz * nxy;
+  auto advance = [&](int64_t& off) {  // plane offset of the next plane (wraps)
+    off += nxy;
+    if (off >= nzxy) off -= nzxy;
+  };
+
+  // copy jobs j = tid, tid + THREADS: in-plane global offsets (wrapped) and
+  // offsets in the slot; phi chunks cover rows y0-2 .., a chunks y0-1 ..
+  int gp[2], ga[2], so[2], gux[2], guy[2], sy8[2];
+  bool hp[2], ha[2], hx[2], hy[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int j = tid + i * THREADS;
+    const int row = j / NCH, ch = j % NCH;
+    const int gx = mod(x0 - 4 + 4 * ch, nx);
+    hp[i] = j < L::NPJ;
+    ha[i] = j < L::NAJ;
+    hx[i] = j < L::NXJ;
+    gp[i] = gx + nx * mod(y0 - 2 + row, ny);
+    ga[i] = gx + nx * mod(y0 - 1 + row, ny);
+    gux[i] = gx + nx * mod(y0 + row, ny);
+    so[i] = row * CW + 4 * ch;
+    const int r8 = j / (TX / 4), c8 = j % (TX / 4);
+    hy[i] = j < L::NYJ;
+    guy[i] = mod(x0 + 4 * c8, nx) + nx * mod(y0 - 1 + r8, ny);
+    sy8[i] = r8 * TX + 4 * c8;
+  }
+  const bool hz = tid < L::NZJ;
+  const int guz = mod(x0 + 4 * (tid % (TX / 4)), nx) + nx * mod(y0 + tid / (TX / 4), ny);
+  auto issue_phi = [&](int64_t zo, int slot) {  // phi and flags of one plane
+    float* sp = s_phi + slot * L::PHI;
+    uint8_t* sf = s_flg + slot * L::FLG;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      if (hp[i]) {
+        cp_async16(sp + so[i], phi + zo + gp[i]);
+        cp_async4(sf + so[i], flags + zo + gp[i]);
+      }
+    }
+  };
+  // a and u_z of the plane at zo, u_x and u_y of the plane before it (zu)
+  auto issue_a = [&](int64_t zo, int64_t zu, int slot) {
+    float* sa = s_a + slot * L::ASLOT;
+    float* su = sa + 3 * L::AC;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      if (ha[i]) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          cp_async16(sa + c * L::AC + so[i], afld + c * N + zo + ga[i]);
+      }
+      if (hx[i]) cp_async16(su + so[i], u + zu + gux[i]);
+      if (hy[i]) cp_async16(su + L::UX + sy8[i], u + N + zu + guy[i]);
+    }
+    if (hz) cp_async16(su + L::UX + L::UY + 4 * tid, u + 2 * N + zo + guz);
+  };
+  auto plane = [&](int p) { return (int64_t)wrap1(p, g.nz) * nxy; };
+
+  // the 2 x 2 nodes of this thread (clamped copies for the global reads of
+  // threads outside the grid)
+  const int x = x0 + 2 * tx;
+  const int ya = y0 + 2 * ty, yb = ya + 1;
+  const bool act_a = (x < nx) && (ya < ny);
+  const bool act_b = (x < nx) && (yb < ny);
+  const int own_a = x + nx * ya, own_b = own_a + nx;  // stores, when active
+  const int cp = (2 * tx + 4) + CW * (2 * ty + 2);  // (x, ya) in the phi window
+  const int ca = (2 * tx + 4) + CW * (2 * ty + 1);  // (x, ya) in the a window
+  const int cux = (2 * tx + 4) + CW * (2 * ty);     // (x, ya) in the u_x window
+  const int cuy = 2 * tx + TX * (2 * ty + 1);       // (x, ya) in the u_y window
+  const int cuz = 2 * tx + TX * (2 * ty);           // (x, ya) in the u_z window
+
+  // prologue: phi planes z0-2, z0-1, then steps 0 .. D-1 (phi t+2, a t+1)
+  const int nb = zend - z0 + 2;  // steps: planes z0-2 .. zend-1 (nb >= 3)
+  issue_phi(plane(z0 - 2), 0);
+  issue_phi(plane(z0 - 1), 1);
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    if (b < nb) {
+      issue_phi(plane(z0 + b), (b + 2) % L::RP);
+      issue_a(plane(z0 - 1 + b), plane(z0 - 2 + b), b % L::RA);
+    }
+    cp_async_commit();
+  }
+  // next issues: phi plane t + 2 + D, a plane t + 1 + D, u plane t + D
+  int64_t zi_phi = plane(z0 + D), zi_a = plane(z0 - 1 + D), zi_u = plane(z0 - 2 + D);
+  int spi = (2 + D) % L::RP, sai = D % L::RA;                 // their slots
+  int sp0 = 0, sa0 = 0;  // phi slot of plane t, a slot of plane t + 1
+  auto next = [](int s, int n) { return s + 1 == n ? 0 : s + 1; };
+
+  QMarch m;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    m.cA[i] = m.cB[i] = make_float2(0.f, 0.f);
+    m.HA[i] = m.HB[i] = m.VA[i] = m.VB[i] = m.LA[i] = m.LB[i] = make_float2(0.f, 0.f);
+  }
+  m.sol = 0u;
+  m.uzA[0] = m.uzA[1] = m.uzB[0] = m.uzB[1] = make_float2(0.f, 0.f);
+  m.szA = m.szB = m.fzmA = m.fzmB = m.fzpA = m.fzpB = make_float2(0.f, 0.f);
+  m.msum = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  m.wsum = m.msum;
+  int64_t zo_u = (int64_t)z0 * nxy;  // output plane of the first emitting step
+
+  // one step: issue the copies D planes ahead, wait for this step's planes,
+  // roll the carried registers and (EMIT) write output plane t
+  auto step = [&](int b, auto first_c, auto emit_c) {
+    constexpr bool FIRST = decltype(first_c)::value;
+    constexpr bool EMIT = decltype(emit_c)::value;
+    if (b + D < nb) {
+      issue_phi(zi_phi, spi);
+      issue_a(zi_a, zi_u, sai);
+    }
+    cp_async_commit();
+    advance(zi_phi);
+    advance(zi_a);
+    advance(zi_u);
+    spi = next(spi, L::RP);
+    sai = next(sai, L::RA);
+    cp_async_wait<D>();
+    __syncthreads();
+    const int sp1 = next(sp0, L::RP), sp2 = next(sp1, L::RP);
+    const float* P0 = s_phi + sp0 * L::PHI;
+    const float* P1 = s_phi + sp1 * L::PHI;
+    const float* P2 = s_phi + sp2 * L::PHI;
+    const uint8_t* S0 = s_flg + sp0 * L::FLG;
+    const uint8_t* S1 = s_flg + sp1 * L::FLG;
+    const float* A1 = s_a + sa0 * L::ASLOT;
+    const float* su = A1 + 3 * L::AC;  // u_x, u_y of plane t, u_z of plane t + 1
+    m.uzA[0] = m.uzA[1];
+    m.uzA[1] = ld2(su + L::UX + L::UY + cuz);
+    m.uzB[0] = m.uzB[1];
+    m.uzB[1] = ld2(su + L::UX + L::UY + cuz + TX);
+    if constexpr (FIRST) {  // own columns at planes z0-2, z0-1
+      m.cA[1] = ld2(P0 + cp);
+      m.cB[1] = ld2(P0 + cp + CW);
+      m.cA[2] = ld2(P1 + cp);
+      m.cB[2] = ld2(P1 + cp + CW);
+    }
+    quad_roll(m, P1, P2, S1, A1, A1 + L::AC, A1 + 2 * L::AC, cp, ca);
+    sp0 = sp1;
+    sa0 = next(sa0, L::RA);
+    if constexpr (EMIT) {
+      // x faces of rows ya and yb
+      const bool sAx = qsolid(m.sol, 1, 0), sAy = qsolid(m.sol, 1, 1);
+      const bool sBx = qsolid(m.sol, 1, 2), sBy = qsolid(m.sol, 1, 3);
+      const float2 dxA = quad_x_faces(ld2(P0 + cp - 2), m.cA[0], ld2(P0 + cp + 2),
+                                      su[cux - 1], ld2(su + cux), su[cux + 2],
+                                      hi_solid(S0 + cp - 2), sAx, sAy,
+                                      lo_solid(S0 + cp + 2));
+      const float2 dxB = quad_x_faces(ld2(P0 + cp + CW - 2), m.cB[0],
+                                      ld2(P0 + cp + CW + 2), su[cux + CW - 1],
+                                      ld2(su + cux + CW), su[cux + CW + 2],
+                                      hi_solid(S0 + cp + CW - 2), sBx, sBy,
+                                      lo_solid(S0 + cp + CW + 2));
+      const float* suy = su + L::UX;
+      const float2 uym = ld2(suy + cuy - TX), uyA = ld2(suy + cuy),
+                   uyB = ld2(suy + cuy + TX), uyp = ld2(suy + cuy + 2 * TX);
+      // y faces ya-1/2, ya+1/2, yb+1/2 of both columns
+      const float2 qm2 = ld2(P0 + cp - 2 * CW), qm1 = ld2(P0 + cp - CW);
+      const float2 qa = m.cA[0], qb = m.cB[0];
+      const float2 qp1 = ld2(P0 + cp + 2 * CW), qp2 = ld2(P0 + cp + 3 * CW);
+      const float2 e0 = vsub(qm1, qm2), e1 = vsub(qa, qm1), e2 = vsub(qb, qa),
+                   e3 = vsub(qp1, qb), e4 = vsub(qp2, qp1);
+      const float2 n0 = neg_part(e0), n1 = neg_part(e1), n2 = neg_part(e2),
+                   n3 = neg_part(e3), n4 = neg_part(e4);
+      const float2 sym = minmod_m(e0, e1, n0, n1), sya = minmod_m(e1, e2, n1, n2),
+                   syb = minmod_m(e2, e3, n2, n3), syp = minmod_m(e3, e4, n3, n4);
+      const float2 fym = face_flux(uym, uyA, qm1, sym, qa, sya);
+      const float2 fyc = face_flux(uyA, uyB, qa, sya, qb, syb);
+      const float2 fyp = face_flux(uyB, uyp, qb, syb, qp1, syp);
+      const uint32_t sm1 = pair_bits(S0 + cp - CW), sp1b = pair_bits(S0 + cp + 2 * CW);
+      const float2 dyA = vsub(masked(sBx, sBy, fyc), masked(sm1 & 1u, sm1 & 2u, fym));
+      const float2 dyB = vsub(masked(sp1b & 1u, sp1b & 2u, fyp), masked(sAx, sAy, fyc));
+      const float2 dzA = vsub(masked(qsolid(m.sol, 2, 0), qsolid(m.sol, 2, 1), m.fzpA),
+                              masked(qsolid(m.sol, 0, 0), qsolid(m.sol, 0, 1), m.fzmA));
+      const float2 dzB = vsub(masked(qsolid(m.sol, 2, 2), qsolid(m.sol, 2, 3), m.fzpB),
+                              masked(qsolid(m.sol, 0, 2), qsolid(m.sol, 0, 3), m.fzmB));
+      float* po = phi_out + zo_u;
+      quad_nodes(m.msum, m.wsum, qa, vadd(vadd(dxA, dyA), dzA), m.LA, m.HA, m.VA, sAx,
+                 sAy, act_a, po + own_a, k);
+      quad_nodes(m.msum, m.wsum, qb, vadd(vadd(dxB, dyB), dzB), m.LB, m.HB, m.VB, sBx,
+                 sBy, act_b, po + own_b, k);
+      zo_u += nxy;
+    }
+  };
+  step(0, std::true_type{}, std::false_type{});
+  step(1, std::false_type{}, std::false_type{});
+#pragma unroll 1
+  for (int b = 2; b < nb; ++b) step(b, std::false_type{}, std::true_type{});
+  cp_async_wait_all();
+  block_partials<THREADS>(df_merge(lane_x(m.msum), lane_y(m.msum)),
+                          df_merge(lane_x(m.wsum), lane_y(m.wsum)), tid, partials, pb,
+                          nblocks);
+}
+
+template <int TYN, int ZC, int D, int MINB>
+__global__ void __launch_bounds__(QTX * TYN / 2, MINB)
+phase_update_quad(const float* __restrict__ phi, const float* __restrict__ afld,
+                  float* __restrict__ phi_out, const float* __restrict__ u,
+                  const uint8_t* __restrict__ flags,
+                  double* __restrict__ partials, int nblocks, Grid g,
+                  Consts k, MassScalars* ms, unsigned* ticket, int zbase, int zlim) {
+  extern __shared__ __align__(16) float dsm[];
+  const int pb = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  phase_tile_quad<TYN, ZC, D>(blockIdx.x, blockIdx.y, blockIdx.z, pb, phi, afld, phi_out,
+                              u, flags, partials, nblocks, g, k, dsm, zbase, zlim);
+  finish_mass(partials, nblocks, ms, ticket, threadIdx.x + QTX * threadIdx.y);
+}
+
 template <int TY, int ZC, int MINB>
 __global__ void __launch_bounds__(TX * TY / 2, MINB)
 phase_update_march(const float* __restrict__ phi, const float* __restrict__ afld,
@@ -842,6 +1351,50 @@ phase_update_batch_copy(const CaseDesc* __restrict__ cases, WorkList wl, int pc)
   }
 }
 
+// 2 x 2 kernels of the four tile shapes (TYN = the tile's rows), with
+// their shared memory
+constexpr int QUAD_D = 1;
+CopyKernel quad_kernel(int variant) {
+  switch (variant) {
+    case 1: return {(void*)phase_update_quad<8, 16, QUAD_D, 5>, QuadTile<8, QUAD_D>::bytes};
+    case 2: return {(void*)phase_update_quad<8, 32, QUAD_D, 5>, QuadTile<8, QUAD_D>::bytes};
+    case 3: return {(void*)phase_update_quad<16, 32, QUAD_D, 3>, QuadTile<16, QUAD_D>::bytes};
+    default: return {(void*)phase_update_quad<16, 16, QUAD_D, 3>, QuadTile<16, QUAD_D>::bytes};
+  }
+}
+
+// Batched phi update over cases that run the 2 x 2 kernel alone.
+template <int TYN, int ZC, int MINB>
+__global__ void __launch_bounds__(QTX * TYN / 2, MINB)
+phase_update_batch_quad(const CaseDesc* __restrict__ cases, WorkList wl, int pc) {
+  extern __shared__ __align__(16) float dsm[];
+  __shared__ CaseCursor cur;
+  if (threadIdx.x == 0 && threadIdx.y == 0) cur.begin();
+  __syncthreads();
+  int b0, b1;
+  block_range(wl, b0, b1);
+  for (int b = b0; b < b1; ++b) {
+    cur.seek(cases, wl, b);
+    const CaseDesc& cd = cur.d;
+    const int local = b - cur.cstart;
+    const int nbx = (cd.g.nx + TX - 1) / TX, nby = (cd.g.ny + TYN - 1) / TYN;
+    __syncthreads();  // the previous tile's shared-memory reads are done
+    phase_tile_quad<TYN, ZC, QUAD_D>(local % nbx, (local / nbx) % nby,
+                                     local / (nbx * nby), local, cd.phi[pc], cd.a,
+                                     cd.phi[1 - pc], cd.u, cd.flags, cd.partials,
+                                     cd.phase_nb, cd.g, cd.k, dsm, 0, cd.g.nz);
+  }
+}
+
+CopyKernel quad_batch_kernel(int variant) {
+  switch (variant) {
+    case 1: return {(void*)phase_update_batch_quad<8, 16, 5>, QuadTile<8, QUAD_D>::bytes};
+    case 2: return {(void*)phase_update_batch_quad<8, 32, 5>, QuadTile<8, QUAD_D>::bytes};
+    case 3: return {(void*)phase_update_batch_quad<16, 32, 3>, QuadTile<16, QUAD_D>::bytes};
+    default: return {(void*)phase_update_batch_quad<16, 16, 3>, QuadTile<16, QUAD_D>::bytes};
+  }
+}
+
 CopyKernel copy_batch_kernel(int variant) {
   switch (variant) {
     case 1: return {(void*)phase_update_batch_copy<8, 16, 4>, CopyTile<8, COPY_D>::bytes};
@@ -854,7 +1407,8 @@ CopyKernel copy_batch_kernel(int variant) {
 
 cudaError_t phase_init_attributes() {
   for (int v = 0; v < 4; ++v) {
-    for (const CopyKernel ck : {copy_kernel(v), copy_batch_kernel(v)}) {
+    for (const CopyKernel ck : {copy_kernel(v), copy_batch_kernel(v), quad_kernel(v),
+                                quad_batch_kernel(v)}) {
       const cudaError_t e = cudaFuncSetAttribute(
           ck.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ck.smem);
       if (e != cudaSuccess) return e;
@@ -877,6 +1431,23 @@ cudaError_t launch_phase_batch_copy(const CaseDesc* cases, WorkList wl, int vari
   const CopyKernel ck = copy_batch_kernel(variant);
   void* args[] = {(void*)&cases, (void*)&wl, (void*)&pc};
   return cudaLaunchKernel(ck.fn, dim3(grid), dim3(TX, s.ty / 2, 1), args, ck.smem,
+                          st);
+}
+
+int phase_batch_quad_occupancy(int variant) {
+  int nb = 0;
+  const PhaseShape s = phase_shape(variant);
+  const CopyKernel ck = quad_batch_kernel(variant);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ck.fn, QTX * s.ty / 2, ck.smem);
+  return nb;
+}
+
+cudaError_t launch_phase_batch_quad(const CaseDesc* cases, WorkList wl, int variant,
+                                    int grid, int pc, cudaStream_t st) {
+  const PhaseShape s = phase_shape(variant);
+  const CopyKernel ck = quad_batch_kernel(variant);
+  void* args[] = {(void*)&cases, (void*)&wl, (void*)&pc};
+  return cudaLaunchKernel(ck.fn, dim3(grid), dim3(QTX, s.ty / 2, 1), args, ck.smem,
                           st);
 }
 
@@ -938,9 +1509,11 @@ cudaError_t launch_phase(cacl_ctx* c, const float* phi_in, float* phi_out) {
   const dim3 block(TX, s.ty / 2, 1);
   const bool copy_ok = phase_copy_ok(c->g, phi_in, phi_out, c->a, c->u, c->flags);
   unsigned* ticket = c->ext_finalize ? nullptr : c->ticket;
-  if (c->phase_pipe == 2 && !copy_ok) return cudaErrorInvalidValue;
+  if (c->phase_pipe >= 2 && !copy_ok) return cudaErrorInvalidValue;
   if (c->phase_pipe != 1 && copy_ok) {
-    const CopyKernel ck = copy_kernel(v);
+    const bool two = c->phase_pipe == 2;  // two nodes per thread along y
+    const CopyKernel ck = two ? copy_kernel(v) : quad_kernel(v);
+    const dim3 cblock = two ? block : dim3(QTX, s.ty / 2, 1);
     const float* a = c->a;
     const float* u = c->u;
     const uint8_t* fl = c->flags;
@@ -954,7 +1527,7 @@ cudaError_t launch_phase(cacl_ctx* c, const float* phi_in, float* phi_out) {
                     (void*)&u,      (void*)&fl,   (void*)&part,
                     (void*)&nbk,    (void*)&g,    (void*)&k,
                     (void*)&ms,     (void*)&ticket, (void*)&zb, (void*)&zl};
-    return cudaLaunchKernel(ck.fn, grid, block, args, ck.smem, c->stream);
+    return cudaLaunchKernel(ck.fn, grid, cblock, args, ck.smem, c->stream);
   }
   switch (v) {
     case 1:
