@@ -250,9 +250,11 @@ struct MassScalars {
 // being rounded away every step.
 __device__ __forceinline__ float add_unbiased(float s, float d, uint32_t step,
                                               uint64_t node) {
-  const float t = s + d;
-  const float bb = t - s;
-  const float e = (s - (t - bb)) + (d - bb);
+  // each operation rounded on its own (a product feeding d must not be
+  // fused into the sum, or the residual is not that of fl(s + d))
+  const float t = __fadd_rn(s, d);
+  const float bb = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(d, bb));
   if (e == 0.f) return t;
   // splitmix64 finalizer of the key
   uint64_t z = ((uint64_t)step << 40) ^ node ^ 0x9E3779B97F4A7C15ull;

@@ -36,15 +36,14 @@ finalize_mass_batch(const CaseDesc* __restrict__ cases) {
   mass_from_partials(cd.partials, cd.phase_nb, cd.mass, threadIdx.x);
 }
 
-// phi = phi* + lambda chi(phi*) at fluid nodes, four nodes per thread,
-// rounded without bias.
-__global__ void __launch_bounds__(ELEM_THREADS)
-correct_phi(float* __restrict__ phi, const uint8_t* __restrict__ flags,
-            const MassScalars* __restrict__ ms, int64_t N, float eps,
-            int64_t node_offset) {
-  const float lam = ms->lambda_f;
-  const uint32_t step = ms->step;
-  const int64_t i4 = ((int64_t)blockIdx.x * ELEM_THREADS + threadIdx.x) * 4;
+// phi = phi* + lambda chi(phi*) at the fluid nodes i4 .. i4 + 3 of a field
+// of N nodes (i4 a multiple of 4), rounded without bias; the rounding key of
+// node n is node_offset + n.
+__device__ __forceinline__ void correct_group(float* __restrict__ phi,
+                                              const uint8_t* __restrict__ flags,
+                                              float lam, uint32_t step, float eps,
+                                              int64_t N, int64_t i4,
+                                              int64_t node_offset) {
   if (i4 + 3 < N) {
     float4 v = *reinterpret_cast<const float4*>(phi + i4);
     const uchar4 fl = *reinterpret_cast<const uchar4*>(flags + i4);
@@ -63,14 +62,23 @@ correct_phi(float* __restrict__ phi, const uint8_t* __restrict__ flags,
   } else {
     for (int64_t n = i4; n < N; ++n) {
       const float s = phi[n];
-      const float chi = (s > eps && s < 1.0f - eps) ? s * (1.0f - s) : 0.0f;
-      if (!(flags[n] & FLAG_SOLID)) phi[n] = add_unbiased(s, lam * chi, step, node_offset + n);
+      if ((s > eps && s < 1.0f - eps) && !(flags[n] & FLAG_SOLID))
+        phi[n] = add_unbiased(s, lam * (s * (1.0f - s)), step, node_offset + n);
     }
   }
 }
 
+// The correction over one field, four nodes per thread.
+__global__ void __launch_bounds__(ELEM_THREADS)
+correct_phi(float* __restrict__ phi, const uint8_t* __restrict__ flags,
+            const MassScalars* __restrict__ ms, int64_t N, float eps,
+            int64_t node_offset) {
+  const int64_t i4 = ((int64_t)blockIdx.x * ELEM_THREADS + threadIdx.x) * 4;
+  correct_group(phi, flags, ms->lambda_f, ms->step, eps, N, i4, node_offset);
+}
+
 // Batched correction: virtual block b covers 4 * ELEM_THREADS nodes of its
-// case.
+// case, four per thread as in correct_phi.
 __global__ void __launch_bounds__(ELEM_THREADS)
 correct_phi_batch(const CaseDesc* __restrict__ cases, WorkList wl, int pc) {
   __shared__ CaseCursor cur;
@@ -81,20 +89,9 @@ correct_phi_batch(const CaseDesc* __restrict__ cases, WorkList wl, int pc) {
   for (int b = b0; b < b1; ++b) {
     cur.seek(cases, wl, b);
     const CaseDesc& cd = cur.d;
-    const float lam = cd.mass->lambda_f;
-    const uint32_t step = cd.mass->step;
-    const float eps = cd.k.eps_phi;
-    float* phi = cd.phi[1 - pc];
-    const int64_t base = (int64_t)(b - cur.cstart) * 4 * ELEM_THREADS;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t n = base + j * ELEM_THREADS + threadIdx.x;
-      if (n < cd.g.N && !(cd.flags[n] & FLAG_SOLID)) {
-        const float s = phi[n];
-        const float chi = (s > eps && s < 1.0f - eps) ? s * (1.0f - s) : 0.0f;
-        phi[n] = add_unbiased(s, lam * chi, step, n);
-      }
-    }
+    const int64_t i4 = ((int64_t)(b - cur.cstart) * ELEM_THREADS + threadIdx.x) * 4;
+    correct_group(cd.phi[1 - pc], cd.flags, cd.mass->lambda_f, cd.mass->step,
+                  cd.k.eps_phi, cd.g.N, i4, 0);
   }
 }
 
