@@ -322,7 +322,12 @@ def run_batched(args, torch, cacl, stream):
         view.set_geometry(solid)
         view.set_fields(phi, u)
     del cases
-    best = b.autotune(steps=2)
+    if args.batch_variant:
+        lv, pv = (int(v) for v in args.batch_variant.split(","))
+        b.set_option(lv, pv)
+        best = {"lb_variant": lv, "phase_variant": pv, "set": "--batch-variant"}
+    else:
+        best = b.autotune(steps=2)
     k = max(4, args.steps // 20)
     b.step(2)
     torch.cuda.synchronize()
@@ -395,6 +400,13 @@ def run_adjoint(args, torch, cacl, stream):
     s.adjoint_backward(g, dth, dsg)
     ev[5].record(stream)
     torch.cuda.synchronize()
+    t_bwd_first = ev[4].elapsed_time(ev[5])
+    # the steady state of an optimisation loop: the backward again (the
+    # segment graphs captured by the first call are replayed)
+    ev[4].record(stream)
+    s.adjoint_backward(g, dth, dsg)
+    ev[5].record(stream)
+    torch.cuda.synchronize()
     t_plain = ev[0].elapsed_time(ev[1])
     t_fwd = ev[2].elapsed_time(ev[3])
     t_bwd = ev[4].elapsed_time(ev[5])
@@ -409,11 +421,14 @@ def run_adjoint(args, torch, cacl, stream):
             "forward_ms_per_step": t_plain / steps,
             "checkpointed_forward_ms_per_step": t_fwd / steps,
             "backward_ms_per_step": t_bwd / steps,
+            "first_backward_ms_per_step": t_bwd_first / steps,
             "backward_over_forward": t_bwd / t_plain,
             "recompute_ms_per_step": t_rec / steps,
             "adjoint_over_forward_excluding_recompute": (t_bwd - t_rec) / t_plain,
-            "note": "backward includes the recompute of every segment with its tape; "
-                    "the second ratio leaves that recompute out"}
+            "note": "backward (second call, as in an optimisation loop; the first "
+                    "call also captures the segment graphs) includes the recompute of "
+                    "every segment with its tape; the second ratio leaves that "
+                    "recompute out"}
 
 
 def run_theta_recovery(args):
@@ -870,6 +885,8 @@ def main():
     ap.add_argument("--c2-steps", type=int, default=60)
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched impact sweep and print its JSON")
+    ap.add_argument("--batch-variant", default="",
+                    help="LB,PHASE launch shapes of the batch instead of autotuning")
     args = ap.parse_args()
     if args.inference:
         run_inference(args)

@@ -58,12 +58,22 @@ adj_correct_sum(const float* __restrict__ phib, const float* __restrict__ phis,
   if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
 }
 
-// S / W and lambda for the apply pass, once per step: one warp sums the
-// block partials of S in a fixed order.
-__global__ void __launch_bounds__(32)
+// S / W and lambda for the apply pass, once per step: one block sums the
+// block partials of S in a fixed order (thread i adds partials i, i + AT,
+// ..., then a fixed tree over the threads).
+__global__ void __launch_bounds__(AT)
 adj_correct_scalars(const double* __restrict__ partial, int nparts,
                     const MassScalars* __restrict__ ms, float* __restrict__ out) {
-  const double S = warp_sum_fixed(partial, nparts, threadIdx.x);
+  __shared__ double sh[AT];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += AT) v += __ldcg(partial + i);
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = AT / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double S = sh[0];
   if (threadIdx.x == 0) {
     const double W = ms->w_sum;
     out[0] = (W > 0.0) ? (float)(S / W) : 0.f;
@@ -761,11 +771,20 @@ struct AdjointState {
   int npart = 0;
   int32_t *row_start = nullptr, *row_entry = nullptr;
   bool forward_done = false;
+  // CUDA graphs of the backward steps of one full-length segment (every
+  // segment but the first one processed), by which of fb / fb2 holds the
+  // later step's adjoints when it starts (slot 0: the lower address); valid
+  // while graph_key (the constants, sizes and context buffers the launches
+  // bake in) matches
+  cudaGraphExec_t seg_graph[2] = {nullptr, nullptr};
+  std::vector<unsigned char> graph_key;
 };
 
 namespace cacl {
 void adjoint_free(AdjointState* s) {
   if (!s) return;
+  for (auto& gx : s->seg_graph)
+    if (gx) cudaGraphExecDestroy(gx);
   for (auto* v : {&s->ck_f, &s->ck_phi, &s->ck1_f, &s->ck1_phi, &s->t_fprev,
                   &s->t_phipre, &s->t_phig, &s->t_u, &s->t_a, &s->t_phis})
     for (float* p : *v) cudaFree(p);
@@ -1024,6 +1043,86 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
   const bool small = (int64_t)Q * N < (int64_t)INT32_MAX;  // 32-bit offsets
   const bool small15 = (int64_t)15 * N < (int64_t)INT32_MAX;  // face buffer
   bool first = true;  // no later step: dL/df* of the final populations is 0
+  // the launches of backward step t of a segment of len steps
+  auto back_step = [&](int t, int len) -> cudaError_t {
+    // A1 correction; S was summed by the ghost gather of the step after this
+    // one within the segment, else here
+    int nparts = nblk(N, AT);
+    if (t == len - 1) {
+      nparts = std::min(nblk(N, AT), 1024);
+      adj_correct_sum<<<nparts, AT, 0, st>>>(s->phib, s->t_phis[t], c->flags, N, eps,
+                                             s->partial);
+    }
+    adj_correct_scalars<<<1, AT, 0, st>>>(s->partial, nparts, s->t_mass + t, s->scal);
+    adj_correct_apply<<<nblk(N, AT), AT, 0, st>>>(s->phib, s->t_phis[t], c->flags, N,
+                                                  eps, s->scal, s->phisb);
+    // A2 phi update
+    const dim3 rows((g.nx + 127) / 128, g.ny, g.nz);
+    if (small15) {
+      adj_phase_faces<int><<<rows, 128, 0, st>>>(s->t_phig[t], s->t_u[t], c->flags,
+                                                 s->phisb, s->face, g);
+      adj_phase_gather<int><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face, s->phigb,
+                                                  s->ub, s->ab, g, c->k);
+    } else {
+      adj_phase_faces<int64_t><<<rows, 128, 0, st>>>(s->t_phig[t], s->t_u[t], c->flags,
+                                                     s->phisb, s->face, g);
+      adj_phase_gather<int64_t><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face,
+                                                      s->phigb, s->ub, s->ab, g, c->k);
+    }
+    // A3 collide-stream; the later step's pulled-population adjoints (none
+    // after the last step)
+    const float* later = first ? nullptr : s->fb;
+    if (small) {
+      adj_lb_node<int><<<rows, 128, 0, st>>>(s->t_fprev[t], s->t_phig[t], c->flags, later,
+                                             s->ub, s->ab, s->fb2, s->nodeb, s->sig_acc, g,
+                                             c->k, db4, dkp);
+    } else {
+      adj_lb_node<int64_t><<<rows, 128, 0, st>>>(s->t_fprev[t], s->t_phig[t], c->flags,
+                                                 later, s->ub, s->ab, s->fb2, s->nodeb,
+                                                 s->sig_acc, g, c->k, db4, dkp);
+    }
+    std::swap(s->fb, s->fb2);  // fb: this step's pulled-population adjoints
+    first = false;
+    if (small)
+      adj_lb_gather<int><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
+    else
+      adj_lb_gather<int64_t><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
+    // A4 ghost map
+    if (W > 0)
+      adj_ghost_node<<<nblk(W, 128), 128, 0, st>>>(s->t_phipre[t], c->w_idx, c->w_donor,
+                                                   c->w_q, c->w_nw, c->w_cot, c->w_theta,
+                                                   s->phigb, s->wd, s->thetab, W, g);
+    adj_ghost_gather<<<nblk(N, AT), AT, 0, st>>>(c->flags, s->phigb, s->row_start,
+                                                 s->row_entry, s->wd, s->phib, N,
+                                                 t > 0 ? s->t_phis[t - 1] : nullptr, eps,
+                                                 s->partial);
+    return cudaGetLastError();
+  };
+
+  // everything the captured segment graphs bake in
+  {
+    std::vector<unsigned char> key;
+    auto put = [&](const void* p, size_t n) {
+      const unsigned char* b = static_cast<const unsigned char*>(p);
+      key.insert(key.end(), b, b + n);
+    };
+    put(&c->k, sizeof(Consts));
+    put(&eps, sizeof eps);
+    put(&db4, sizeof db4);
+    put(&dkp, sizeof dkp);
+    const int64_t dims[] = {g.nx, g.ny, g.nz, g.N, W, s->every};
+    put(dims, sizeof dims);
+    const void* bufs[] = {c->flags, c->w_idx, c->w_donor, c->w_q, c->w_nw, c->w_cot,
+                          c->w_theta};
+    put(bufs, sizeof bufs);
+    if (key != s->graph_key) {
+      for (auto& gx : s->seg_graph) {
+        if (gx) cudaGraphExecDestroy(gx);
+        gx = nullptr;
+      }
+      s->graph_key = key;
+    }
+  }
   // outer segments, last first (one segment spanning the rollout with one
   // level); with two levels each is recomputed once from its outer
   // checkpoint to rebuild its inner checkpoints
@@ -1077,60 +1176,34 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
       float ms = 0.f;
       ACK(cudaEventElapsedTime(&ms, ev_a, ev_b), "event");
       s->t_recompute_ms += ms;
-      for (int t = len - 1; t >= 0; --t) {
-        // A1 correction; S was summed by the ghost gather of the step after
-        // this one within the segment, else here
-        int nparts = nblk(N, AT);
-        if (t == len - 1) {
-          nparts = std::min(nblk(N, AT), 1024);
-          adj_correct_sum<<<nparts, AT, 0, st>>>(s->phib, s->t_phis[t], c->flags, N, eps,
-                                                 s->partial);
-        }
-        adj_correct_scalars<<<1, 32, 0, st>>>(s->partial, nparts, s->t_mass + t, s->scal);
-        adj_correct_apply<<<nblk(N, AT), AT, 0, st>>>(s->phib, s->t_phis[t], c->flags,
-                                                      N, eps, s->scal, s->phisb);
-        // A2 phi update
-        const dim3 rows((g.nx + 127) / 128, g.ny, g.nz);
-        if (small15) {
-          adj_phase_faces<int><<<rows, 128, 0, st>>>(s->t_phig[t], s->t_u[t], c->flags,
-                                                     s->phisb, s->face, g);
-          adj_phase_gather<int><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face,
-                                                      s->phigb, s->ub, s->ab, g, c->k);
-        } else {
-          adj_phase_faces<int64_t><<<rows, 128, 0, st>>>(s->t_phig[t], s->t_u[t],
-                                                         c->flags, s->phisb, s->face, g);
-          adj_phase_gather<int64_t><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face,
-                                                          s->phigb, s->ub, s->ab, g,
-                                                          c->k);
-        }
-        // A3 collide-stream
-        // the later step's pulled-population adjoints (none after the last)
-        const float* later = first ? nullptr : s->fb;
-        if (small) {
-          adj_lb_node<int><<<rows, 128, 0, st>>>(s->t_fprev[t], s->t_phig[t], c->flags,
-                                                 later, s->ub, s->ab, s->fb2, s->nodeb,
-                                                 s->sig_acc, g, c->k, db4, dkp);
-        } else {
-          adj_lb_node<int64_t><<<rows, 128, 0, st>>>(
-              s->t_fprev[t], s->t_phig[t], c->flags, later, s->ub, s->ab, s->fb2,
-              s->nodeb, s->sig_acc, g, c->k, db4, dkp);
-        }
-        std::swap(s->fb, s->fb2);  // fb: this step's pulled-population adjoints
-        first = false;
-        if (small)
-          adj_lb_gather<int><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
-        else
-          adj_lb_gather<int64_t><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
-        // A4 ghost map
-        if (W > 0)
-          adj_ghost_node<<<nblk(W, 128), 128, 0, st>>>(
-              s->t_phipre[t], c->w_idx, c->w_donor, c->w_q, c->w_nw, c->w_cot,
-              c->w_theta, s->phigb, s->wd, s->thetab, W, g);
-        adj_ghost_gather<<<nblk(N, AT), AT, 0, st>>>(
-            c->flags, s->phigb, s->row_start, s->row_entry, s->wd, s->phib, N,
-            t > 0 ? s->t_phis[t - 1] : nullptr, eps, s->partial);
-        ACK(cudaGetLastError(), "adjoint step");
+      const bool use_graph = !first && len == s->every;
+      if (!use_graph) {
+        for (int t = len - 1; t >= 0; --t) ACK(back_step(t, len), "adjoint step");
+        continue;
       }
+      const int slot = s->fb < s->fb2 ? 0 : 1;
+      if (!s->seg_graph[slot]) {
+        // capture the segment's backward steps once; the host-side state
+        // they change (fb / fb2) is put back and replayed below
+        float* const fb0 = s->fb;
+        float* const fb20 = s->fb2;
+        ACK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "capture");
+        cudaError_t ce = cudaSuccess;
+        for (int t = len - 1; t >= 0 && ce == cudaSuccess; --t) ce = back_step(t, len);
+        cudaGraph_t gr = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(st, &gr);
+        s->fb = fb0;
+        s->fb2 = fb20;
+        if (ce != cudaSuccess || ee != cudaSuccess) {
+          if (gr) cudaGraphDestroy(gr);
+          ACK(ce != cudaSuccess ? ce : ee, "capture adjoint segment");
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&s->seg_graph[slot], gr, 0);
+        cudaGraphDestroy(gr);
+        ACK(ie, "instantiate adjoint segment");
+      }
+      ACK(cudaGraphLaunch(s->seg_graph[slot], st), "adjoint segment");
+      if (len % 2) std::swap(s->fb, s->fb2);  // one swap per replayed step
     }
   }
   sum_partials<<<1, 128, 0, st>>>(s->sig_acc, nbl_all, s->sigmab);
