@@ -216,6 +216,36 @@ cacl_status cacl_check_finite(cacl_ctx* ctx);
 cacl_status cacl_adjoint_forward(cacl_ctx* ctx, int nsteps, int ckpt_every);
 cacl_status cacl_adjoint_backward(cacl_ctx* ctx, const float* dL_dphi,
                                   double* dL_dtheta, double* dL_dsigma);
+/* One stage of the adjoint on its own (a test hook for the transposes):
+ * step 0 of the rollout of the last cacl_adjoint_forward (one level) is
+ * recomputed from its checkpoint, and the transpose of one of its maps is
+ * applied to the cotangent `in` at that linearisation point. All pointers
+ * are device pointers (FP32 unless stated), node-major as the fields:
+ *   CACL_ADJ_CORRECT (Sect. 2.3, Eq. mass_corrected_phi with lambda of
+ *     Eq. mass_correction_normalization): in = phi^{n+1}_bar (N) ->
+ *     out = phi*_bar (N).
+ *   CACL_ADJ_PHASE (Sect. 2.1.1, Eq. phi_update_muscl, the compressive
+ *     vector a taken as an input): in = phi*_bar (N) -> out = [phi_g_bar
+ *     (N) | u_bar (3N) | a_bar (3N)].
+ *   CACL_ADJ_COLLIDE (Sect. 2.1, Eqs. lbe .. lap_iso, the compressive vector
+ *     of the ghosted phi and the pull of the next step): in = [the next
+ *     step's pulled populations' cotangent (27N) | u_bar (3N) | a_bar (3N)]
+ *     -> out = [this step's pulled populations' cotangent (27N) |
+ *     phi_g_bar (N)], dparam[0] = dL/dsigma (double).
+ *   CACL_ADJ_GHOST (Sect. 2.2): in = phi_g_bar (N) -> out = phi^n_bar (N),
+ *     dparam = dL/dtheta per wall node (W doubles, wall-list order).
+ * state (optional, 36 N floats) receives the linearisation point: phi^n,
+ * f*^{n-1} (27 N, as stored), the ghosted phi, u, a, phi*. The context's
+ * state is left as it was. CACL_ERR_STATE without a one-level forward. */
+typedef enum {
+  CACL_ADJ_CORRECT = 0,
+  CACL_ADJ_PHASE = 1,
+  CACL_ADJ_COLLIDE = 2,
+  CACL_ADJ_GHOST = 3
+} cacl_adj_stage;
+cacl_status cacl_adjoint_stage(cacl_ctx* ctx, int stage, const float* in, float* out,
+                               double* dparam, float* state);
+
 /* GPU time (CUDA events) of the last cacl_adjoint_backward: the taped
  * recomputes of its segments (and outer segments) and the whole call, in
  * milliseconds. CACL_ERR_STATE before any backward. */

@@ -169,12 +169,24 @@ class TorchStep:
         gval = phi_f + lam * (gc * self.w_rfs).sum(1)
         return flat.index_put((self.w_idx,), gval).reshape(self.shape)
 
+    def pull(self, f):
+        """Sect. 2.1: the populations a node pulls, f_q(x - c_q), with
+        halfway bounce-back f_q(x) = f_opp(q)(x) where x - c_q is solid."""
+        pulled = torch.stack([at(f[i], -C_[i]) for i in range(27)])
+        return torch.where(self.bb, f[OPP], pulled)
+
     def collide(self, f, phi, sigma):
         """Sect. 2.1: pull with halfway bounce-back, then the regularised
-        collision with the Guo source of F = F_sigma + F_p + F_ext + F_nu."""
+        collision; solid nodes keep their populations."""
+        fout, u = self.collide_pulled(self.pull(f), phi, sigma)
+        return torch.where(self.solid, f, fout), u
+
+    def collide_pulled(self, fin, phi, sigma):
+        """Sect. 2.1: the regularised collision of the pulled populations
+        with the Guo source of F = F_sigma + F_p + F_ext + F_nu; returns the
+        post-collision populations (meaningful at fluid nodes) and u (0 at
+        solid nodes)."""
         p = self.p
-        pulled = torch.stack([at(f[i], -C_[i]) for i in range(27)])
-        fin = torch.where(self.bb, f[OPP], pulled)
         g = grad_iso(phi)
         lap = lap_iso(phi)
         drho = p["rho_l"] - p["rho_g"]
@@ -208,9 +220,8 @@ class TorchStep:
         fneq = bcast(WT, fin) * (torch.einsum("iab,ab...->i...", H2, A2) / (2 * CS2 ** 2)
                                  + torch.einsum("iabg,abg...->i...", H3, A3) / (6 * CS2 ** 3))
         fout = feq + (1.0 - omega) * fneq + 0.5 * S
-        f_new = torch.where(self.solid, f, fout)
         u = torch.where(self.solid, torch.zeros_like(u), u)
-        return f_new, u
+        return fout, u
 
     def compressive(self, phi):
         """a = phi (1 - phi) grad phi / |grad phi| at fluid nodes; 0 at solid
@@ -225,8 +236,9 @@ class TorchStep:
             h = torch.where(band, h, h.detach())
         return torch.where(ok, phi * (1.0 - phi) * h, torch.zeros_like(h))
 
-    def phase(self, phi, u):
-        """Sect. 2.1.1, Eq. phi_update_muscl at fluid nodes."""
+    def phase(self, phi, u, a=None):
+        """Sect. 2.1.1, Eq. phi_update_muscl at fluid nodes; a: the
+        compressive vector (formed from phi when not given)."""
         p = self.p
         kappa = 4.0 * p["mobility"] / p["width"]
         div = torch.zeros_like(phi)
@@ -242,7 +254,8 @@ class TorchStep:
             flux = uf * torch.where(uf >= 0, phiL, phiR)
             flux = torch.where(self.solid | r_sol, torch.zeros_like(flux), flux)
             div = div + flux - at(flux, em)
-        a = self.compressive(phi)
+        if a is None:
+            a = self.compressive(phi)
         diva = torch.zeros_like(phi)
         for i in range(27):
             ca = sum(C_[i][k] * at(a[k], C_[i]) for k in range(3) if C_[i][k] != 0)

@@ -32,12 +32,13 @@ EXPORTS = (
     "cacl_batch_case", "cacl_batch_step", "cacl_batch_set_option",
     "cacl_batch_autotune", "cacl_set_wall_angles", "cacl_set_sigma",
     "cacl_adjoint_forward", "cacl_adjoint_forward_levels", "cacl_adjoint_backward",
-    "cacl_adjoint_timing", "cacl_slab_create", "cacl_slab_stage", "cacl_slab_partials", "cacl_slab_correct",
+    "cacl_adjoint_timing", "cacl_adjoint_stage", "cacl_slab_create", "cacl_slab_stage", "cacl_slab_partials", "cacl_slab_correct",
     "cacl_slab_halo", "cacl_slab_halo_bytes",
 )
 OPT_PHASE_TILE = 1
 OPT_PHASE_PIPE = 2  # 0 auto, 1 registers, 2 copies (2 nodes/thread), 3 copies (2 x 2)
 OPT_LB_PIPE = 3  # 0 direct loads, 1 bulk-copy staged rows
+ADJ_CORRECT, ADJ_PHASE, ADJ_COLLIDE, ADJ_GHOST = 0, 1, 2, 3  # cacl_adjoint_stage
 
 
 class CaclError(RuntimeError):
@@ -116,6 +117,7 @@ def load():
     L.cacl_adjoint_forward_levels.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     L.cacl_adjoint_backward.argtypes = [vp, vp, vp, vp]
     L.cacl_adjoint_timing.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.cacl_adjoint_stage.argtypes = [vp, C.c_int, vp, vp, vp, vp]
     L.cacl_slab_create.argtypes = [C.POINTER(CaclParams), C.c_int, C.c_int, vp,
                                    C.POINTER(vp)]
     L.cacl_slab_stage.argtypes = [vp, C.c_int]
@@ -372,6 +374,19 @@ class Solver:
         self._check(self.L.cacl_adjoint_backward(
             self.h, C.c_void_p(dl_dphi.data_ptr()), C.c_void_p(dl_dtheta.data_ptr()),
             C.c_void_p(dl_dsigma.data_ptr())))
+
+    def adjoint_stage(self, stage, cot_in, out, dparam=None, state=None):
+        """One stage's transpose at step 0 of the last forward (test hook,
+        cacl_adjoint_stage): device torch tensors, float32 cot_in / out /
+        state, float64 dparam."""
+        import torch
+        for t, dt in ((cot_in, torch.float32), (out, torch.float32), (dparam, torch.float64),
+                      (state, torch.float32)):
+            if t is not None and (not t.is_cuda or t.dtype != dt or not t.is_contiguous()):
+                raise ValueError("adjoint_stage: contiguous CUDA tensors of the stated dtypes")
+        ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        self._check(self.L.cacl_adjoint_stage(self.h, int(stage), ptr(cot_in), ptr(out),
+                                              ptr(dparam), ptr(state)))
 
     def adjoint_timing(self):
         """GPU milliseconds of the last backward: (recompute, total)."""

@@ -1236,6 +1236,142 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
   return CACL_OK;
 }
 
+cacl_status cacl_adjoint_stage(cacl_ctx* c, int stage, const float* in, float* out,
+                               double* dparam, float* state) {
+  if (!c || stage < CACL_ADJ_CORRECT || stage > CACL_ADJ_GHOST || !in || !out)
+    return c ? afail(c, CACL_ERR_ARG, "invalid adjoint stage request") : CACL_ERR_ARG;
+  AdjointState* s = c->adj;
+  if (!s || !s->forward_done || s->outer != 0)
+    return afail(c, CACL_ERR_STATE, "call cacl_adjoint_forward first (one level)");
+  const Grid g = c->g;
+  const int64_t N = g.N;
+  const int W = s->W;
+  const float eps = c->k.eps_phi;
+  const double width = c->p.width;
+  const float db4 = (float)(48.0 / width), dkp = (float)(1.5 * width);
+  cudaStream_t st = c->stream;
+  const size_t pb = sizeof(float) * N;
+  // step 0 of the rollout, recomputed from checkpoint 0 into tape slot 0;
+  // the context's state is saved and put back
+  float* save_f = nullptr;
+  float* save_phi = nullptr;
+  ACK(alloc(&save_f, (size_t)Q * N), "alloc");
+  ACK(alloc(&save_phi, N), "alloc");
+  ACK(cudaMemcpyAsync(save_f, c->f[c->fcur], pb * Q, cudaMemcpyDeviceToDevice, st), "save");
+  ACK(cudaMemcpyAsync(save_phi, c->phi[c->pcur], pb, cudaMemcpyDeviceToDevice, st), "save");
+  const int save_fc = c->fcur, save_pc = c->pcur;
+  MassScalars save_mass;
+  ACK(cudaMemcpyAsync(&save_mass, c->mass, sizeof(MassScalars), cudaMemcpyDeviceToHost, st),
+      "save");
+  ACK(cudaStreamSynchronize(st), "sync");
+  ACK(cudaMemcpyAsync(s->t_fprev[0], s->ck_f[0], pb * Q, cudaMemcpyDeviceToDevice, st),
+      "restore");
+  ACK(cudaMemcpyAsync(c->phi[c->pcur], s->ck_phi[0], pb, cudaMemcpyDeviceToDevice, st),
+      "restore");
+  ACK(cudaMemcpyAsync(c->mass, s->ck_mass, sizeof(MassScalars), cudaMemcpyDeviceToDevice, st),
+      "restore");
+  const cacl_status ts = taped_step(c, s, 0, 1);
+  if (ts != CACL_OK) return ts;
+  if (state) {  // the linearisation point
+    float* o = state;
+    const float* parts[] = {s->t_phipre[0], s->t_fprev[0], s->t_phig[0], s->t_u[0],
+                            s->t_a[0], s->t_phis[0]};
+    const size_t sizes[] = {1, Q, 1, 3, 3, 1};
+    for (int i = 0; i < 6; ++i) {
+      ACK(cudaMemcpyAsync(o, parts[i], pb * sizes[i], cudaMemcpyDeviceToDevice, st), "state");
+      o += sizes[i] * N;
+    }
+  }
+  const dim3 rows((g.nx + 127) / 128, g.ny, g.nz);
+  const bool small = (int64_t)Q * N < (int64_t)INT32_MAX;
+  const bool small15 = (int64_t)15 * N < (int64_t)INT32_MAX;
+  switch (stage) {
+    case CACL_ADJ_CORRECT: {
+      ACK(cudaMemcpyAsync(s->phib, in, pb, cudaMemcpyDeviceToDevice, st), "in");
+      const int nparts = std::min(nblk(N, AT), 1024);
+      adj_correct_sum<<<nparts, AT, 0, st>>>(s->phib, s->t_phis[0], c->flags, N, eps,
+                                             s->partial);
+      adj_correct_scalars<<<1, AT, 0, st>>>(s->partial, nparts, s->t_mass, s->scal);
+      adj_correct_apply<<<nblk(N, AT), AT, 0, st>>>(s->phib, s->t_phis[0], c->flags, N,
+                                                    eps, s->scal, s->phisb);
+      ACK(cudaMemcpyAsync(out, s->phisb, pb, cudaMemcpyDeviceToDevice, st), "out");
+      break;
+    }
+    case CACL_ADJ_PHASE:
+      ACK(cudaMemcpyAsync(s->phisb, in, pb, cudaMemcpyDeviceToDevice, st), "in");
+      if (small15) {
+        adj_phase_faces<int><<<rows, 128, 0, st>>>(s->t_phig[0], s->t_u[0], c->flags,
+                                                   s->phisb, s->face, g);
+        adj_phase_gather<int><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face, s->phigb,
+                                                    s->ub, s->ab, g, c->k);
+      } else {
+        adj_phase_faces<int64_t><<<rows, 128, 0, st>>>(s->t_phig[0], s->t_u[0], c->flags,
+                                                       s->phisb, s->face, g);
+        adj_phase_gather<int64_t><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face,
+                                                        s->phigb, s->ub, s->ab, g, c->k);
+      }
+      ACK(cudaMemcpyAsync(out, s->phigb, pb, cudaMemcpyDeviceToDevice, st), "out");
+      ACK(cudaMemcpyAsync(out + N, s->ub, 3 * pb, cudaMemcpyDeviceToDevice, st), "out");
+      ACK(cudaMemcpyAsync(out + 4 * N, s->ab, 3 * pb, cudaMemcpyDeviceToDevice, st), "out");
+      break;
+    case CACL_ADJ_COLLIDE: {
+      ACK(cudaMemcpyAsync(s->fb, in, pb * Q, cudaMemcpyDeviceToDevice, st), "in");
+      ACK(cudaMemcpyAsync(s->ub, in + Q * N, 3 * pb, cudaMemcpyDeviceToDevice, st), "in");
+      ACK(cudaMemcpyAsync(s->ab, in + (Q + 3) * N, 3 * pb, cudaMemcpyDeviceToDevice, st),
+          "in");
+      const int nbl_all = (int)(((g.nx + 127) / 128) * (int64_t)g.ny * g.nz);
+      ACK(cudaMemsetAsync(s->sig_acc, 0, sizeof(double) * nbl_all, st), "zero");
+      ACK(cudaMemsetAsync(s->phigb, 0, pb, st), "zero");
+      if (small) {
+        adj_lb_node<int><<<rows, 128, 0, st>>>(s->t_fprev[0], s->t_phig[0], c->flags, s->fb,
+                                               s->ub, s->ab, s->fb2, s->nodeb, s->sig_acc,
+                                               g, c->k, db4, dkp);
+        adj_lb_gather<int><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
+      } else {
+        adj_lb_node<int64_t><<<rows, 128, 0, st>>>(s->t_fprev[0], s->t_phig[0], c->flags,
+                                                   s->fb, s->ub, s->ab, s->fb2, s->nodeb,
+                                                   s->sig_acc, g, c->k, db4, dkp);
+        adj_lb_gather<int64_t><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
+      }
+      sum_partials<<<1, 128, 0, st>>>(s->sig_acc, nbl_all, s->sigmab);
+      ACK(cudaMemcpyAsync(out, s->fb2, pb * Q, cudaMemcpyDeviceToDevice, st), "out");
+      ACK(cudaMemcpyAsync(out + Q * N, s->phigb, pb, cudaMemcpyDeviceToDevice, st), "out");
+      if (dparam)
+        ACK(cudaMemcpyAsync(dparam, s->sigmab, sizeof(double), cudaMemcpyDeviceToDevice, st),
+            "out");
+      break;
+    }
+    default:  // CACL_ADJ_GHOST
+      ACK(cudaMemcpyAsync(s->phigb, in, pb, cudaMemcpyDeviceToDevice, st), "in");
+      ACK(cudaMemsetAsync(s->thetab, 0, sizeof(double) * (W > 0 ? W : 1), st), "zero");
+      if (W > 0)
+        adj_ghost_node<<<nblk(W, 128), 128, 0, st>>>(s->t_phipre[0], c->w_idx, c->w_donor,
+                                                     c->w_q, c->w_nw, c->w_cot, c->w_theta,
+                                                     s->phigb, s->wd, s->thetab, W, g);
+      adj_ghost_gather<<<nblk(N, AT), AT, 0, st>>>(c->flags, s->phigb, s->row_start,
+                                                   s->row_entry, s->wd, s->phib, N, nullptr,
+                                                   eps, s->partial);
+      ACK(cudaMemcpyAsync(out, s->phib, pb, cudaMemcpyDeviceToDevice, st), "out");
+      if (dparam && W > 0)
+        ACK(cudaMemcpyAsync(dparam, s->thetab, sizeof(double) * W, cudaMemcpyDeviceToDevice,
+                            st), "out");
+      break;
+  }
+  ACK(cudaGetLastError(), "adjoint stage");
+  c->fcur = save_fc;
+  c->pcur = save_pc;
+  ACK(cudaMemcpyAsync(c->f[c->fcur], save_f, pb * Q, cudaMemcpyDeviceToDevice, st),
+      "restore");
+  ACK(cudaMemcpyAsync(c->phi[c->pcur], save_phi, pb, cudaMemcpyDeviceToDevice, st),
+      "restore");
+  ACK(cudaMemcpyAsync(c->mass, &save_mass, sizeof(MassScalars), cudaMemcpyHostToDevice, st),
+      "restore");
+  ACK(cudaStreamSynchronize(st), "sync");
+  cudaFree(save_f);
+  cudaFree(save_phi);
+  return CACL_OK;
+}
+
 cacl_status cacl_adjoint_timing(const cacl_ctx* c, double* recompute_ms,
                                 double* total_ms) {
   if (!c || !c->adj) return CACL_ERR_STATE;
