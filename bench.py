@@ -192,6 +192,53 @@ def cpu_oracle_run(steps, max_seconds=30.0):
             f"{dt:.1f} s")
 
 
+def cpu_case_time(kind, steps):
+    """Seconds and node updates of the FP64 oracle on one of the paper-shaped
+    cases: "c1" the 2D static droplet (128 x 64, D2Q9), "c2" the 128^3
+    spreading case, "slab" the headline's 256 x 256 x 64 lower slab."""
+    from oracle import oracle as O
+    from paper_2607_25444_b300 import inputs as I
+    if kind == "c1":
+        p, solid, phi = I.static_droplet_2d(60.0)
+    elif kind == "c2":
+        p, solid, phi = I.spreading_128(60.0)
+    else:
+        n, nz = GRID, 64
+        p = I.base_params(n, n, nz, sigma=0.02, theta_deg=THETA)
+        solid = I.walls_z(n, n, nz)
+        phi = I.droplet(n, n, nz, (n / 2, n / 2, 0.5), 40.0, p["width"])
+    o = O.Oracle(p)
+    o.set_geometry(solid)
+    o.set_fields(phi.astype(np.float64))
+    t0 = time.perf_counter()
+    o.step(steps)
+    return time.perf_counter() - t0, phi.size * steps
+
+
+def run_cpu_extended(args):
+    """The oracle on the host cores beyond the bench's bounded sample: the
+    headline slab on one thread and on all threads, the 2D c1 case at its
+    full length (2000 steps) and a 10-step sample of c2, each in a child
+    process with its OpenMP thread count set."""
+    import subprocess
+    cores = len(os.sched_getaffinity(0))
+    cases = [("slab", 1, 1), ("slab", 1, cores), ("c1", 2000, cores),
+             ("c1", 2000, 1), ("c2", 10, cores)]
+    out = []
+    for kind, steps, threads in cases:
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+        code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+                "t, n = bench.cpu_case_time(%r, %d); print(json.dumps([t, n]))"
+                % (ROOT, kind, steps))
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                           text=True, check=True)
+        t, n = json.loads(r.stdout.strip().splitlines()[-1])
+        out.append({"case": kind, "steps": steps, "threads": threads, "seconds": t,
+                    "mlups": n / t / 1e6})
+    print(json.dumps({"metric": "FP64 oracle MLUPS on the host cores", "cores": cores,
+                      "runs": out}), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -686,6 +733,12 @@ def run_cuda(args):
     s = cacl.Solver(p)
     s.set_geometry(solid)
     s.set_fields(phi)
+    if args.phase_tile is not None:
+        s.set_option(cacl.OPT_PHASE_TILE, args.phase_tile)
+    if args.phase_pipe is not None:
+        s.set_option(cacl.OPT_PHASE_PIPE, args.phase_pipe)
+    if args.lb_pipe is not None:
+        s.set_option(cacl.OPT_LB_PIPE, args.lb_pipe)
     W = s.info()["wall_count"]
     # collide-stream, phi update (its last block forms lambda), correction,
     # and the two ghost passes when there are walls
@@ -789,6 +842,14 @@ def run_cuda(args):
         v, cores, sample = cpu_oracle_run(2, max_seconds=30.0)
         cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": sample}
+    options = {k: v for k, v in (("phase_tile", args.phase_tile),
+                                 ("phase_pipe", args.phase_pipe),
+                                 ("lb_pipe", args.lb_pipe)) if v is not None}
+    if args.lb_pipe in (1, 2, 3):
+        lb_kernel = {1: "lb_collide_staged", 2: "lb_collide", 3: "lb_collide_tma"}[args.lb_pipe]
+    else:
+        lb_kernel = {"f32": "lb_collide_pair32", "f16": "lb_collide_quad",
+                     "bf16": "lb_collide_quad", "moments": "lb_collide_moments"}[args.storage]
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "repeats": args.repeats,
@@ -804,11 +865,13 @@ def run_cuda(args):
                    "grid": [args.grid] * 3, "storage": args.storage,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (populations 2 x 1.8 GB)",
-                   "wall_nodes": W, "fluid_nodes": fluid},
+                   "wall_nodes": W, "fluid_nodes": fluid,
+                   **({"options": options} if options else {})},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": kernel_traffic(fluid) if args.storage == "f32" else None,
-                     "kernel": "lb_collide_pair32" if args.storage == "f32" else "lb_collide",
+                     "traffic": (kernel_traffic(fluid)
+                                 if lb_kernel == "lb_collide_pair32" else None),
+                     "kernel": lb_kernel,
                      "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": lb_bytes,
                      "kernel_bytes_per_fluid_node": lb_bytes_fluid(args.storage) + 12,
@@ -883,8 +946,17 @@ def main():
                     help="storage-mode error on the 128^3 spreading case "
                          "against the FP64 oracle instead")
     ap.add_argument("--c2-steps", type=int, default=60)
+    ap.add_argument("--cpu-extended", action="store_true",
+                    help="time the FP64 oracle on the host: headline slab on 1 and all "
+                         "threads, c1 at 2000 steps, 10 steps of c2")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched impact sweep and print its JSON")
+    ap.add_argument("--phase-tile", type=int, default=None,
+                    help="CACL_OPT_PHASE_TILE of the headline solver")
+    ap.add_argument("--phase-pipe", type=int, default=None,
+                    help="CACL_OPT_PHASE_PIPE of the headline solver")
+    ap.add_argument("--lb-pipe", type=int, default=None,
+                    help="CACL_OPT_LB_PIPE of the headline solver")
     ap.add_argument("--batch-variant", default="",
                     help="LB,PHASE launch shapes of the batch instead of autotuning")
     args = ap.parse_args()
@@ -893,6 +965,9 @@ def main():
         return
     if args.c2_accuracy:
         run_c2_accuracy(args)
+        return
+    if args.cpu_extended:
+        run_cpu_extended(args)
         return
     if args.batch_only:
         import torch
