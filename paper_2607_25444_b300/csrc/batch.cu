@@ -25,14 +25,19 @@ struct cacl_batch {
   CaseDesc* d_cases = nullptr;
   int* d_starts = nullptr;  // NLISTS lists of ncases + 1 starts
   // collide-stream: the cases of one, two and four nodes per thread
-  // (wl_lb[0..2]); phi update: cases staged through registers (wl_phase),
-  // by copies with two nodes per thread (wl_phase_copy) and with 2 x 2
-  // (wl_phase_quad); each as the case would run alone
-  WorkList wl_lb[3]{}, wl_phase{}, wl_phase_copy{}, wl_phase_quad{}, wl_ghost{},
-      wl_corr{};
+  // (wl_lb[w], w = 0, 1, 2); phi update: the cases of width class w staged
+  // through registers (wl_ph[0][w]), by copies with two nodes per thread
+  // (wl_ph[1][w]) and with 2 x 2 (wl_ph[2][w]); each as the case would run
+  // alone
+  WorkList wl_lb[3]{}, wl_ph[3][3]{}, wl_ghost{}, wl_corr{};
   int grid_lb[3] = {0, 0, 0};
-  int grid_phase = 0, grid_phase_copy = 0, grid_phase_quad = 0, grid_ghost = 0,
-      grid_corr = 0;
+  int grid_ph[3][3] = {};
+  int grid_ghost = 0, grid_corr = 0;
+  // the width classes touch disjoint cases: in the captured step each runs
+  // its collide-stream and phi update as a branch of its own (side streams
+  // joined by events), between the ghost update and the correction
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool plan_ok = false;
   std::vector<int> geom_version;  // of each case when the plan was built
@@ -42,7 +47,7 @@ struct cacl_batch {
 
 namespace {
 
-constexpr int NLISTS = 8;
+constexpr int NLISTS = 14;  // ghost, correction, 3 collide-stream, 3 x 3 phi
 constexpr int LB_WIDTH[3] = {1, 2, 4};
 
 cacl_status bfail(cacl_batch* b, cacl_status st, const std::string& msg) {
@@ -79,12 +84,13 @@ cacl_status build_plan(cacl_batch* b) {
   b->phase_nb.assign(nc, 0);
   b->geom_version.assign(nc, -1);
   std::vector<int> starts(NLISTS * (nc + 1), 0);
-  int* s_ph = starts.data();
-  int* s_gh = s_ph + (nc + 1);
-  int* s_cr = s_gh + (nc + 1);
-  int* s_pc = s_cr + (nc + 1);
-  int* s_lb[3] = {s_pc + (nc + 1), s_pc + 2 * (nc + 1), s_pc + 3 * (nc + 1)};
-  int* s_pq = s_pc + 4 * (nc + 1);
+  auto list = [&](int k) { return starts.data() + k * (nc + 1); };
+  int* s_gh = list(0);
+  int* s_cr = list(1);
+  int* s_lb[3] = {list(2), list(3), list(4)};
+  int* s_ph[3][3];
+  for (int q = 0; q < 3; ++q)
+    for (int w = 0; w < 3; ++w) s_ph[q][w] = list(5 + 3 * q + w);
   const int row = lb_batch_row(b->lb_variant);
   int ty = 16, zc = 16;
   phase_tile(b->phase_variant, ty, zc);
@@ -131,10 +137,10 @@ cacl_status build_plan(cacl_batch* b) {
     }
     const bool copy = c->phase_pipe != 1 &&
                       phase_copy_ok(c->g, c->phi[0], c->phi[1], c->a, c->u, c->flags);
-    const bool two = copy && c->phase_pipe == 2;  // else 2 x 2
-    s_ph[i + 1] = s_ph[i] + (copy ? 0 : d.phase_nb);
-    s_pc[i + 1] = s_pc[i] + (two ? d.phase_nb : 0);
-    s_pq[i + 1] = s_pq[i] + (copy && !two ? d.phase_nb : 0);
+    const int pipe = !copy ? 0 : (c->phase_pipe == 2 ? 1 : 2);
+    for (int q = 0; q < 3; ++q)
+      for (int w = 0; w < 3; ++w)
+        s_ph[q][w][i + 1] = s_ph[q][w][i] + (q == pipe && w == wc ? d.phase_nb : 0);
     s_gh[i + 1] = s_gh[i] + (c->wall_count + ghost_batch_block() - 1) /
                                 ghost_batch_block();
     const int64_t per = correct_batch_nodes();
@@ -145,13 +151,13 @@ cacl_status build_plan(cacl_batch* b) {
   BCK(cudaMemcpyAsync(b->d_starts, starts.data(), sizeof(int) * starts.size(),
                       cudaMemcpyHostToDevice, b->stream), "upload work-lists");
   BCK(cudaStreamSynchronize(b->stream), "sync");
-  b->wl_phase = {b->d_starts, nc, s_ph[nc]};
-  b->wl_ghost = {b->d_starts + (nc + 1), nc, s_gh[nc]};
-  b->wl_corr = {b->d_starts + 2 * (nc + 1), nc, s_cr[nc]};
-  b->wl_phase_copy = {b->d_starts + 3 * (nc + 1), nc, s_pc[nc]};
-  for (int w = 0; w < 3; ++w)
-    b->wl_lb[w] = {b->d_starts + (4 + w) * (nc + 1), nc, s_lb[w][nc]};
-  b->wl_phase_quad = {b->d_starts + 7 * (nc + 1), nc, s_pq[nc]};
+  auto dlist = [&](int k) { return b->d_starts + k * (nc + 1); };
+  b->wl_ghost = {dlist(0), nc, s_gh[nc]};
+  b->wl_corr = {dlist(1), nc, s_cr[nc]};
+  for (int w = 0; w < 3; ++w) b->wl_lb[w] = {dlist(2 + w), nc, s_lb[w][nc]};
+  for (int q = 0; q < 3; ++q)
+    for (int w = 0; w < 3; ++w)
+      b->wl_ph[q][w] = {dlist(5 + 3 * q + w), nc, s_ph[q][w][nc]};
   // persistent grids: as many blocks as stay resident, at most the work
   const int sms = sm_count();
   auto grid_for = [&](int total, int per_sm) {
@@ -166,15 +172,25 @@ cacl_status build_plan(cacl_batch* b) {
                    ? grid_for(b->wl_lb[w].total,
                               lb_batch_occupancy(b->storage, LB_WIDTH[w], b->lb_variant))
                    : b->wl_lb[w].total);
-  b->grid_phase = grid_for(b->wl_phase.total, phase_batch_occupancy(b->phase_variant));
-  b->grid_phase_copy =
-      grid_for(b->wl_phase_copy.total, phase_batch_copy_occupancy(b->phase_variant));
-  b->grid_phase_quad =
-      grid_for(b->wl_phase_quad.total, phase_batch_quad_occupancy(b->phase_variant));
+  const int occ[3] = {phase_batch_occupancy(b->phase_variant),
+                      phase_batch_copy_occupancy(b->phase_variant),
+                      phase_batch_quad_occupancy(b->phase_variant)};
+  for (int q = 0; q < 3; ++q)
+    for (int w = 0; w < 3; ++w) b->grid_ph[q][w] = grid_for(b->wl_ph[q][w].total, occ[q]);
   b->grid_ghost = grid_for(b->wl_ghost.total, 8);
   b->grid_corr = grid_for(b->wl_corr.total, 8);
   b->plan_ok = true;
   return CACL_OK;
+}
+
+// phi-update launch of pipeline q (0 registers, 1 two-node copies, 2 2 x 2)
+cudaError_t launch_phase_pipe(const CaseDesc* cases, WorkList wl, int q, int variant,
+                              int grid, int pc, cudaStream_t st) {
+  switch (q) {
+    case 0: return launch_phase_batch(cases, wl, variant, grid, pc, st);
+    case 1: return launch_phase_batch_copy(cases, wl, variant, grid, pc, st);
+    default: return launch_phase_batch_quad(cases, wl, variant, grid, pc, st);
+  }
 }
 
 cudaError_t enqueue_batch_step(cacl_batch* b, int par) {
@@ -182,24 +198,34 @@ cudaError_t enqueue_batch_step(cacl_batch* b, int par) {
   if ((e = launch_ghost_batch(b->d_cases, b->wl_ghost, b->grid_ghost, par,
                               b->stream)) != cudaSuccess)
     return e;
-  for (int w = 0; w < 3; ++w)
-    if (b->wl_lb[w].total > 0 &&
-        (e = launch_lb_batch(b->d_cases, b->wl_lb[w], b->storage, LB_WIDTH[w],
-                             b->lb_variant, b->grid_lb[w], par, par, b->stream)) !=
-            cudaSuccess)
+  // one branch per collide-stream width class: its collide-stream, then the
+  // phi update of the same cases; the first branch on the batch's stream
+  if ((e = cudaEventRecord(b->ev_fork, b->stream)) != cudaSuccess) return e;
+  int nside = 0;
+  bool main_used = false;
+  for (int w = 0; w < 3; ++w) {
+    if (b->wl_lb[w].total == 0) continue;
+    cudaStream_t sw = b->stream;
+    if (main_used) {
+      sw = b->side[nside];
+      if ((e = cudaStreamWaitEvent(sw, b->ev_fork, 0)) != cudaSuccess) return e;
+    }
+    if ((e = launch_lb_batch(b->d_cases, b->wl_lb[w], b->storage, LB_WIDTH[w],
+                             b->lb_variant, b->grid_lb[w], par, par, sw)) != cudaSuccess)
       return e;
-  if (b->wl_phase.total > 0 &&
-      (e = launch_phase_batch(b->d_cases, b->wl_phase, b->phase_variant,
-                              b->grid_phase, par, b->stream)) != cudaSuccess)
-    return e;
-  if (b->wl_phase_copy.total > 0 &&
-      (e = launch_phase_batch_copy(b->d_cases, b->wl_phase_copy, b->phase_variant,
-                                   b->grid_phase_copy, par, b->stream)) != cudaSuccess)
-    return e;
-  if (b->wl_phase_quad.total > 0 &&
-      (e = launch_phase_batch_quad(b->d_cases, b->wl_phase_quad, b->phase_variant,
-                                   b->grid_phase_quad, par, b->stream)) != cudaSuccess)
-    return e;
+    for (int q = 0; q < 3; ++q)
+      if (b->wl_ph[q][w].total > 0 &&
+          (e = launch_phase_pipe(b->d_cases, b->wl_ph[q][w], q, b->phase_variant,
+                                 b->grid_ph[q][w], par, sw)) != cudaSuccess)
+        return e;
+    if (main_used) {
+      if ((e = cudaEventRecord(b->ev_join[nside], sw)) != cudaSuccess) return e;
+      ++nside;
+    }
+    main_used = true;
+  }
+  for (int k = 0; k < nside; ++k)
+    if ((e = cudaStreamWaitEvent(b->stream, b->ev_join[k], 0)) != cudaSuccess) return e;
   return launch_correct_batch(b->d_cases, (int)b->cases.size(), b->wl_corr,
                               b->grid_corr, par, b->stream);
 }
@@ -255,6 +281,17 @@ cacl_status cacl_batch_create(const cacl_params* params, int ncases,
     }
     b->cases.push_back(c);
   }
+  for (int k = 0; k < 2; ++k) {
+    if (cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) != cudaSuccess) {
+      cacl_batch_destroy(b);
+      return CACL_ERR_CUDA;
+    }
+  }
+  if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+    cacl_batch_destroy(b);
+    return CACL_ERR_CUDA;
+  }
   if (cudaMalloc(&b->d_cases, sizeof(CaseDesc) * ncases) != cudaSuccess ||
       cudaMalloc(&b->d_starts, sizeof(int) * NLISTS * (ncases + 1)) != cudaSuccess) {
     cacl_batch_destroy(b);
@@ -271,6 +308,11 @@ void cacl_batch_destroy(cacl_batch* b) {
   for (cacl_ctx* c : b->cases) cacl_destroy(c);
   if (b->d_cases) cudaFree(b->d_cases);
   if (b->d_starts) cudaFree(b->d_starts);
+  for (int k = 0; k < 2; ++k) {
+    if (b->side[k]) cudaStreamDestroy(b->side[k]);
+    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
