@@ -1,5 +1,6 @@
 """Parity at the benchmark's full size (256^3 static droplet, the launch
-configuration bench.py times): one step of the GPU state after 100 steps is
+configuration bench.py times) and at 432^3, where 27 N exceeds 2^31 and the
+collide-stream runs its 64-bit-offset kernel: one step of the GPU state after 100 steps is
 compared, node by node, with the oracle stepping 14^3 windows cut from that
 state around sampled nodes (bulk, interface, contact line); the interior of
 each window beyond the reach of one step (5 nodes) is checked. The global
@@ -19,7 +20,8 @@ def _window_idx(lo, n, size=WIN):
     return (np.arange(lo, lo + size) % n).astype(np.int64)
 
 
-def test_fullsize_one_step_windows():
+@pytest.mark.parametrize("n", [256, 432])
+def test_fullsize_one_step_windows(n):
     import sys
 
     import torch
@@ -27,8 +29,7 @@ def test_fullsize_one_step_windows():
     sys.path.insert(0, __file__.rsplit("/tests/", 1)[0])
     import bench
     from paper_2607_25444_b300 import cacl
-    p, solid, phi = bench.workload(256)
-    n = 256
+    p, solid, phi = bench.workload(n)
     s = cacl.Solver(p)
     s.set_geometry(solid)
     s.set_fields(phi)
@@ -57,9 +58,12 @@ def test_fullsize_one_step_windows():
     ph0v, phsv, u1v = ph0.view(n, n, n), phs.view(n, n, n), u1.view(3, n, n, n)
 
     # sampled window origins (z0, y0, x0): contact line, interface, bulk
-    origins = [(0, 128 - 7, 128 + 40 - 7), (0, 128 - 7, 128 - 40 - 7),
-               (0, 128 + 28 - 7, 128 + 28 - 7), (20, 128 + 22 - 7, 128 - 7),
-               (30, 100, 100), (120, 10, 200), (240, 50, 60), (0, 0, 0)]
+    sc = lambda v: int(round(v * n / 256))
+    c, R = n // 2, sc(40)
+    origins = [(0, c - 7, c + R - 7), (0, c - 7, c - R - 7),
+               (0, c + sc(28) - 7, c + sc(28) - 7), (sc(20), c + sc(22) - 7, c - 7),
+               (sc(30), sc(100), sc(100)), (sc(120), sc(10), sc(200)),
+               (n - 16, sc(50), sc(60)), (0, 0, 0)]
     worst = dict(phi=0.0, u=0.0, f=0.0)
     for (z0, y0, x0) in origins:
         zi, yi, xi = _window_idx(z0, n), _window_idx(y0, n), _window_idx(x0, n)
@@ -95,7 +99,7 @@ def test_fullsize_one_step_windows():
             max(np.abs(rf[(slice(None),) + core][:, fl]).max(), 1e-9)
         worst = {k: max(worst[k], v) for k, v in
                  dict(phi=e_phi, u=e_u, f=e_f).items()}
-    print("full-size window parity", worst)
+    print(f"full-size window parity at {n}^3", worst)
     assert worst["phi"] < 1e-5 and worst["u"] < 1e-4 and worst["f"] < 1e-5, worst
 
     # the volume correction: lambda from FP64 sums of the whole phi*
