@@ -284,17 +284,18 @@ def time_lb_kernel(solver, torch, reps):
     return start.elapsed_time(end) / reps / 1e3
 
 
-def impact_sweep_cases(ncases=48, storage="f16"):
+def impact_sweep_cases(ncases=48, storage="f16", pick=None):
     """Batched impact sweep shaped like the paper's Sect. 3.3: 48 cubes with
     edges drawn from [64, 160], a drop of radius 0.2 n resting on the bottom
     wall with a downward speed set by a Weber number drawn from [1, 80],
     contact angle drawn from [120, 160] deg, density ratio 100, FP16
-    storage; seeded draws."""
+    storage; seeded draws (pick: indices of the draws to build)."""
     import math as _m
 
     from paper_2607_25444_b300 import inputs as I
     out = []
-    for d in I.impact_sweep(ncases):
+    draws = I.impact_sweep(ncases)
+    for d in (draws if pick is None else [draws[i] for i in pick]):
         n = d["n"]
         p = I.base_params(n, n, n, sigma=0.003, rho_l=1.0, rho_g=0.01,
                           nu_l=0.03, nu_g=0.03, theta_deg=d["theta_deg"],

@@ -99,3 +99,36 @@ def test_autotune_and_lockstep():
     with pytest.raises(cacl.CaclError):
         b.step(1)
     b.close()
+
+
+def test_sweep_cases_batch_equals_alone():
+    """Six cases of the batched impact sweep (edges 69, 70, 78, 80, 87 and
+    96: every collide-stream width and phi-update pipeline, FP16 storage,
+    the drop moving toward the wall) after 10 steps: the batch, with its
+    width classes as concurrent branches, gives bit for bit what each case
+    gives alone."""
+    import sys
+
+    sys.path.insert(0, __file__.rsplit("/tests/", 1)[0])
+    import bench
+    from paper_2607_25444_b300 import cacl
+    cases = bench.impact_sweep_cases(pick=[8, 47, 11, 5, 23, 28])
+    assert sorted(c[0]["nx"] % 4 for c in cases) == [0, 0, 1, 2, 2, 3]
+    b = cacl.Batch([c[0] for c in cases])
+    b.set_option(1, 2)
+    for view, (p, solid, phi, u) in zip(b.cases, cases):
+        view.set_geometry(solid)
+        view.set_fields(phi, u)
+    b.step(10)
+    for view, (p, solid, phi, u) in zip(b.cases, cases):
+        s = cacl.Solver(p)
+        s.set_option(cacl.OPT_PHASE_TILE, 2)
+        s.set_geometry(solid)
+        s.set_fields(phi, u)
+        s.step(10)
+        for x, y in zip(view.fields(), s.fields()):
+            assert np.array_equal(x, y)
+        assert np.array_equal(view.populations(), s.populations())
+        assert view.mass()["lam"] == s.mass()["lam"]
+        s.close()
+    b.close()
