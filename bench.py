@@ -507,6 +507,13 @@ def run_theta_recovery(args):
         m = s.mass()
         f = s.fields()[0].astype(np.float64)
         rec["mass_drift_rel"] = abs(f[solid == 0].sum() - m["m_ref"]) / m["m_ref"]
+        # sensitivity of the measured angle to the unstated wall position
+        # z_w and to the fit (crossings on z >= 1 against the band of nodes
+        # with |phi - 1/2| < 0.1 and 0.2)
+        rec["z_wall"] = {str(zw): Dg.contact_angle(f, zw, z_min=1.0)
+                         for zw in (0.0, 0.5, 1.0)}
+        rec["band_fit"] = {str(e): Dg.contact_angle_band(f, e, 0.5, z_min=1.0)
+                           for e in (0.1, 0.2)}
         out.append(rec)
         s.close()
         print(json.dumps(rec), flush=True)

@@ -71,6 +71,22 @@ def contact_angle(phi, z_wall=0.5, y=None, z_min=None):
     return math.degrees(math.pi - math.acos(arg))
 
 
+def contact_angle_band(phi, eps_fit=0.1, z_wall=0.5, y=None, z_min=None):
+    """The same angle from the circle fitted to the node centres of the
+    slice y with |phi - 1/2| < eps_fit (the band fit of Eq.
+    measured_contact_angle) instead of the interpolated crossings."""
+    nz, ny, nx = phi.shape
+    sl = np.asarray(phi[:, ny // 2 if y is None else y, :], dtype=np.float64)
+    iz, ix = np.nonzero(np.abs(sl - 0.5) < eps_fit)
+    x, z = ix.astype(np.float64), iz.astype(np.float64)
+    if z_min is not None:
+        keep = z >= z_min
+        x, z = x[keep], z[keep]
+    x0, z0, R = fit_circle(x, z)
+    arg = min(1.0, max(-1.0, (z0 - z_wall) / R))
+    return math.degrees(math.pi - math.acos(arg))
+
+
 def footprint_radius(phi, layer=1):
     """r = sqrt(A / pi), A the area of phi > 1/2 on a fluid layer."""
     return math.sqrt(float((phi[layer] > 0.5).sum()) / math.pi)

@@ -22,6 +22,15 @@ def test_contact_angle_of_exact_caps():
         assert abs(D.contact_angle(_cap(th), 0.5, z_min=1.0) - th) < 0.5
 
 
+def test_band_fit_of_exact_caps():
+    """The band fit (node centres with |phi - 1/2| < eps) recovers the cap's
+    angle; it reads a band of nodes around the crossing, so it is checked
+    to 1.5 deg."""
+    for th in (40.0, 90.0, 140.0):
+        for eps in (0.1, 0.2):
+            assert abs(D.contact_angle_band(_cap(th), eps, 0.5, z_min=1.0) - th) < 1.5
+
+
 def test_footprint_of_a_disc():
     n = 101
     y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
