@@ -157,6 +157,30 @@ cacl_status cacl_set_phi(cacl_ctx* ctx, const float* phi);
 cacl_status cacl_set_velocity(cacl_ctx* ctx, const float* u);
 cacl_status cacl_set_mass_ref(cacl_ctx* ctx, double m_ref);
 
+/* Checkpoint and resume. cacl_save_state copies the complete dynamic state
+ * of the context into a host buffer of at least cacl_state_bytes bytes: a
+ * header (grid, storage, wall count), the current populations as stored,
+ * phi with its ghost values, u, the mass record of the volume correction
+ * (M_ref, the last M*, W and lambda, and the count of corrections, which
+ * keys their unbiased rounding) and the contact angle of every wall node.
+ * cacl_load_state restores it into a context of the same grid, storage and
+ * geometry (cacl_set_geometry first); stepping on from there gives bit for
+ * bit what the saved context gives. The caller owns the buffer and any
+ * file it is written to. cacl_state_bytes returns -1 before
+ * cacl_set_geometry; save returns CACL_ERR_STATE before cacl_set_fields,
+ * CACL_ERR_ARG for a short buffer; load returns CACL_ERR_ARG for a buffer
+ * that is not a saved state or belongs to another grid, storage or
+ * geometry. Both synchronise the context stream. */
+int64_t cacl_state_bytes(const cacl_ctx* ctx);
+cacl_status cacl_save_state(cacl_ctx* ctx, void* host_buf, int64_t bytes);
+cacl_status cacl_load_state(cacl_ctx* ctx, const void* host_buf, int64_t bytes);
+
+/* Test hook for failure detection: sets the context's device error word as
+ * a bounded wait for asynchronous copies that gave up would (no GPU fault
+ * is made); the next cacl_check_finite then returns CACL_ERR_TIMEOUT. The
+ * word stays set: the state is not trusted after such a failure. */
+cacl_status cacl_inject_wait_timeout(cacl_ctx* ctx);
+
 /* Advance nsteps >= 0 full steps (ghost update, collide-stream, phi update,
  * volume correction) on the context stream; does not synchronise. */
 cacl_status cacl_step(cacl_ctx* ctx, int nsteps);

@@ -32,7 +32,8 @@ EXPORTS = (
     "cacl_batch_case", "cacl_batch_step", "cacl_batch_set_option",
     "cacl_batch_autotune", "cacl_set_wall_angles", "cacl_set_sigma",
     "cacl_adjoint_forward", "cacl_adjoint_forward_levels", "cacl_adjoint_backward",
-    "cacl_adjoint_timing", "cacl_adjoint_stage", "cacl_slab_create", "cacl_slab_stage", "cacl_slab_partials", "cacl_slab_correct",
+    "cacl_adjoint_timing", "cacl_adjoint_stage", "cacl_state_bytes", "cacl_save_state",
+    "cacl_load_state", "cacl_inject_wait_timeout", "cacl_slab_create", "cacl_slab_stage", "cacl_slab_partials", "cacl_slab_correct",
     "cacl_slab_halo", "cacl_slab_halo_bytes",
 )
 OPT_PHASE_TILE = 1
@@ -118,6 +119,11 @@ def load():
     L.cacl_adjoint_backward.argtypes = [vp, vp, vp, vp]
     L.cacl_adjoint_timing.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.cacl_adjoint_stage.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+    L.cacl_state_bytes.argtypes = [vp]
+    L.cacl_state_bytes.restype = C.c_int64
+    L.cacl_save_state.argtypes = [vp, vp, C.c_int64]
+    L.cacl_load_state.argtypes = [vp, vp, C.c_int64]
+    L.cacl_inject_wait_timeout.argtypes = [vp]
     L.cacl_slab_create.argtypes = [C.POINTER(CaclParams), C.c_int, C.c_int, vp,
                                    C.POINTER(vp)]
     L.cacl_slab_stage.argtypes = [vp, C.c_int]
@@ -387,6 +393,24 @@ class Solver:
         ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
         self._check(self.L.cacl_adjoint_stage(self.h, int(stage), ptr(cot_in), ptr(out),
                                               ptr(dparam), ptr(state)))
+
+    def save_state(self):
+        """The complete dynamic state (cacl_save_state) as a bytes object."""
+        n = self.L.cacl_state_bytes(self.h)
+        if n < 0:
+            raise CaclError(-3, "cacl_state_bytes: set_geometry first")
+        buf = C.create_string_buffer(int(n))
+        self._check(self.L.cacl_save_state(self.h, buf, C.c_int64(n)))
+        return buf.raw
+
+    def load_state(self, state):
+        """Restore a state from save_state (same grid, storage, geometry)."""
+        buf = C.create_string_buffer(bytes(state), len(state))
+        self._check(self.L.cacl_load_state(self.h, buf, C.c_int64(len(state))))
+
+    def inject_wait_timeout(self):
+        """Test hook: mark the context as if a copy wait had given up."""
+        self._check(self.L.cacl_inject_wait_timeout(self.h))
 
     def adjoint_timing(self):
         """GPU milliseconds of the last backward: (recompute, total)."""

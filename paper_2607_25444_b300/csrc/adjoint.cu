@@ -912,6 +912,7 @@ cacl_status cacl_adjoint_forward_levels(cacl_ctx* c, int nsteps, int every,
   if (!c->has_fields) return afail(c, CACL_ERR_STATE, "set_fields first");
   if (c->p.storage != CACL_F32)
     return afail(c, CACL_ERR_ARG, "the adjoint needs FP32 population storage");
+  NvtxRange range("cacl_adjoint_forward");
   if (c->fcur != c->pcur) return afail(c, CACL_ERR_STATE, "step parts out of phase");
   const int64_t N = c->g.N;
   AdjointState* s = c->adj;
@@ -1003,6 +1004,7 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
   AdjointState* s = c->adj;
   if (!s || !s->forward_done)
     return afail(c, CACL_ERR_STATE, "call cacl_adjoint_forward first");
+  NvtxRange range("cacl_adjoint_backward");
   const Grid g = c->g;
   const int64_t N = g.N;
   const int W = s->W;

@@ -343,6 +343,7 @@ cacl_status cacl_set_mass_ref(cacl_ctx* c, double m) {
 cacl_status cacl_step(cacl_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return fail(c, CACL_ERR_ARG, "invalid step count");
   if (!ready(c)) return CACL_ERR_STATE;
+  cacl::NvtxRange range("cacl_step");
   for (int s = 0; s < nsteps; ++s) {
     cudaGraphExec_t& gx = c->graph[c->fcur][c->pcur];
     if (!gx) CK(build_graph(c, c->fcur, c->pcur), "capture step");
@@ -350,6 +351,120 @@ cacl_status cacl_step(cacl_ctx* c, int nsteps) {
     c->fcur ^= 1;
     c->pcur ^= 1;
   }
+  return CACL_OK;
+}
+
+namespace {
+// Layout of a saved state: header, the current populations as stored, the
+// current phi (with ghosts), u, the mass record (64 bytes), the wall angles.
+struct StateHeader {
+  char magic[8];
+  int32_t nx, ny, nz, storage, comps, walls;
+  int64_t nodes;
+  int64_t reserved[3];
+};
+static_assert(sizeof(StateHeader) == 64, "64-byte header");
+constexpr char STATE_MAGIC[8] = {'C', 'A', 'C', 'L', 'S', 'T', '0', '1'};
+constexpr size_t MASS_SLOT = 64;
+static_assert(sizeof(MassScalars) <= MASS_SLOT, "mass record fits its slot");
+
+int64_t state_bytes(const cacl_ctx* c) {
+  const int64_t N = c->g.N;
+  return (int64_t)sizeof(StateHeader) +
+         (int64_t)pop_comps(c->p.storage) * N * (int64_t)storage_bytes(c->p.storage) +
+         4 * N * (int64_t)sizeof(float) + (int64_t)MASS_SLOT +
+         (int64_t)c->wall_count * (int64_t)sizeof(float);
+}
+}  // namespace
+
+int64_t cacl_state_bytes(const cacl_ctx* c) {
+  if (!c || !c->has_geometry) return -1;
+  return state_bytes(c);
+}
+
+cacl_status cacl_save_state(cacl_ctx* c, void* buf, int64_t bytes) {
+  if (!c || !buf) return fail(c, CACL_ERR_ARG, "null argument");
+  if (!ready(c)) return CACL_ERR_STATE;
+  if (bytes < state_bytes(c)) return fail(c, CACL_ERR_ARG, "state buffer too small");
+  const int64_t N = c->g.N;
+  char* o = static_cast<char*>(buf);
+  StateHeader h{};
+  std::memcpy(h.magic, STATE_MAGIC, sizeof h.magic);
+  h.nx = c->g.nx;
+  h.ny = c->g.ny;
+  h.nz = c->g.nz;
+  h.storage = c->p.storage;
+  h.comps = pop_comps(c->p.storage);
+  h.walls = c->wall_count;
+  h.nodes = N;
+  std::memcpy(o, &h, sizeof h);
+  o += sizeof h;
+  const size_t fb = (size_t)h.comps * N * storage_bytes(c->p.storage);
+  CK(cudaMemcpyAsync(o, c->f[c->fcur], fb, cudaMemcpyDeviceToHost, c->stream), "save f");
+  o += fb;
+  CK(cudaMemcpyAsync(o, c->phi[c->pcur], sizeof(float) * N, cudaMemcpyDeviceToHost,
+                     c->stream), "save phi");
+  o += sizeof(float) * N;
+  CK(cudaMemcpyAsync(o, c->u, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, c->stream),
+     "save u");
+  o += sizeof(float) * 3 * N;
+  std::memset(o, 0, MASS_SLOT);
+  CK(cudaMemcpyAsync(o, c->mass, sizeof(MassScalars), cudaMemcpyDeviceToHost, c->stream),
+     "save mass");
+  o += MASS_SLOT;
+  if (c->wall_count > 0)
+    CK(cudaMemcpyAsync(o, c->w_theta, sizeof(float) * c->wall_count,
+                       cudaMemcpyDeviceToHost, c->stream), "save angles");
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  return CACL_OK;
+}
+
+cacl_status cacl_load_state(cacl_ctx* c, const void* buf, int64_t bytes) {
+  if (!c || !buf) return fail(c, CACL_ERR_ARG, "null argument");
+  if (!c->has_geometry) return fail(c, CACL_ERR_STATE, "set_geometry first");
+  if (bytes < (int64_t)sizeof(StateHeader)) return fail(c, CACL_ERR_ARG, "no state header");
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof h);
+  if (std::memcmp(h.magic, STATE_MAGIC, sizeof h.magic) != 0)
+    return fail(c, CACL_ERR_ARG, "not a saved state");
+  if (h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz || h.storage != c->p.storage ||
+      h.comps != pop_comps(c->p.storage) || h.walls != c->wall_count || h.nodes != c->g.N)
+    return fail(c, CACL_ERR_ARG, "saved state of another grid, storage or geometry");
+  if (bytes < state_bytes(c)) return fail(c, CACL_ERR_ARG, "state buffer too small");
+  const int64_t N = c->g.N;
+  const char* o = static_cast<const char*>(buf) + sizeof h;
+  const size_t fb = (size_t)h.comps * N * storage_bytes(c->p.storage);
+  CK(cudaMemcpyAsync(c->f[0], o, fb, cudaMemcpyHostToDevice, c->stream), "load f");
+  o += fb;
+  for (int i = 0; i < 2; ++i)
+    CK(cudaMemcpyAsync(c->phi[i], o, sizeof(float) * N, cudaMemcpyHostToDevice,
+                       c->stream), "load phi");
+  o += sizeof(float) * N;
+  CK(cudaMemcpyAsync(c->u, o, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, c->stream),
+     "load u");
+  o += sizeof(float) * 3 * N;
+  CK(cudaMemsetAsync(c->a, 0, sizeof(float) * 3 * N, c->stream), "zero a");
+  CK(cudaMemcpyAsync(c->mass, o, sizeof(MassScalars), cudaMemcpyHostToDevice, c->stream),
+     "load mass");
+  o += MASS_SLOT;
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  c->fcur = 0;
+  c->pcur = 0;
+  c->has_fields = true;
+  if (c->wall_count > 0) {
+    const cacl_status st = cacl_set_wall_angles(c, reinterpret_cast<const float*>(o));
+    if (st != CACL_OK) return st;
+  }
+  return CACL_OK;
+}
+
+cacl_status cacl_inject_wait_timeout(cacl_ctx* c) {
+  if (!c) return CACL_ERR_ARG;
+  if (!c->ticket) return fail(c, CACL_ERR_STATE, "context without device state");
+  const unsigned one = 1u;
+  CK(cudaMemcpyAsync(c->ticket + 1, &one, sizeof one, cudaMemcpyHostToDevice, c->stream),
+     "inject");
+  CK(cudaStreamSynchronize(c->stream), "sync");
   return CACL_OK;
 }
 

@@ -342,6 +342,7 @@ cacl_status cacl_batch_set_option(cacl_batch* b, int lb_variant,
 
 cacl_status cacl_batch_step(cacl_batch* b, int nsteps) {
   if (!b || nsteps < 0) return bfail(b, CACL_ERR_ARG, "invalid step count");
+  NvtxRange range("cacl_batch_step");
   const int par = b->cases[0]->fcur;
   for (cacl_ctx* c : b->cases) {
     if (!c->has_fields)

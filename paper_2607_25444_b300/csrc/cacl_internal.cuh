@@ -6,6 +6,7 @@
 // (Sect. 2.1), c_s^2 = 1/3. Everything is derived from q at compile time.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -455,6 +456,15 @@ struct cacl_ctx {
 
 // Kernel launchers (defined in the .cu files). All enqueue on c->stream.
 namespace cacl {
+// An NVTX range around a host call: a profiler's timeline shows the step,
+// batch step and adjoint calls by name.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 cudaError_t launch_geometry(cacl_ctx* c, const uint8_t* solid_dev);
 cudaError_t launch_ghost(cacl_ctx* c, float* phi);
 cudaError_t lb_init(cacl_ctx* c);
