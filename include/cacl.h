@@ -355,12 +355,19 @@ cacl_status cacl_batch_autotune(cacl_batch* batch, int steps, int* lb_variant,
  * 3 = tiles of 128 nodes copied into shared memory and stored back by the
  * tensor memory accelerator (when nx is a multiple of 8; else as 0); all
  * bit-identical at fluid nodes (the tiled form writes f* = 0 at solid
- * nodes, the others leave them). Defaults: tile 2, pipelines 0.
+ * nodes, the others leave them). CACL_OPT_INDEX64 = 1 makes every
+ * collide-stream and adjoint kernel that exists with 32- and 64-bit offsets
+ * take its 64-bit form (and the collide-stream the one-node or staged
+ * kernel, as when 27 N >= 2^31), whatever the grid size; the results are
+ * bit-identical to pipeline 2 (or 1) and to the 32-bit adjoint. It exists so
+ * that the path of grids above 2^31 / 27 nodes can be checked on small
+ * ones. Defaults: tile 2, pipelines 0, index64 0.
  * Returns CACL_ERR_ARG for an unknown option or value. */
 typedef enum {
   CACL_OPT_PHASE_TILE = 1,
   CACL_OPT_PHASE_PIPE = 2,
-  CACL_OPT_LB_PIPE = 3
+  CACL_OPT_LB_PIPE = 3,
+  CACL_OPT_INDEX64 = 4
 } cacl_option;
 cacl_status cacl_set_option(cacl_ctx* ctx, int option, int value);
 

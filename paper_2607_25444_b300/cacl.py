@@ -39,6 +39,7 @@ EXPORTS = (
 OPT_PHASE_TILE = 1
 OPT_PHASE_PIPE = 2  # 0 auto, 1 registers, 2 copies (2 nodes/thread), 3 copies (2 x 2)
 OPT_LB_PIPE = 3  # 0 direct loads, 1 bulk-copy staged rows
+OPT_INDEX64 = 4  # 1: the 64-bit offset forms of the kernels, at any size
 ADJ_CORRECT, ADJ_PHASE, ADJ_COLLIDE, ADJ_GHOST = 0, 1, 2, 3  # cacl_adjoint_stage
 
 

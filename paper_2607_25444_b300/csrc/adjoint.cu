@@ -1042,8 +1042,8 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
   const int nbl_all = (int)(((g.nx + 127) / 128) * (int64_t)g.ny * g.nz);
   ACK(cudaMemsetAsync(s->sig_acc, 0, sizeof(double) * nbl_all, st), "seed");
 
-  const bool small = (int64_t)Q * N < (int64_t)INT32_MAX;  // 32-bit offsets
-  const bool small15 = (int64_t)15 * N < (int64_t)INT32_MAX;  // face buffer
+  const bool small = !c->index64 && (int64_t)Q * N < (int64_t)INT32_MAX;  // 32-bit offsets
+  const bool small15 = !c->index64 && (int64_t)15 * N < (int64_t)INT32_MAX;  // face buffer
   bool first = true;  // no later step: dL/df* of the final populations is 0
   // the launches of backward step t of a segment of len steps
   auto back_step = [&](int t, int len) -> cudaError_t {
@@ -1112,7 +1112,7 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
     put(&eps, sizeof eps);
     put(&db4, sizeof db4);
     put(&dkp, sizeof dkp);
-    const int64_t dims[] = {g.nx, g.ny, g.nz, g.N, W, s->every};
+    const int64_t dims[] = {g.nx, g.ny, g.nz, g.N, W, s->every, c->index64 ? 1 : 0};
     put(dims, sizeof dims);
     const void* bufs[] = {c->flags, c->w_idx, c->w_donor, c->w_q, c->w_nw, c->w_cot,
                           c->w_theta};
@@ -1285,8 +1285,8 @@ cacl_status cacl_adjoint_stage(cacl_ctx* c, int stage, const float* in, float* o
     }
   }
   const dim3 rows((g.nx + 127) / 128, g.ny, g.nz);
-  const bool small = (int64_t)Q * N < (int64_t)INT32_MAX;
-  const bool small15 = (int64_t)15 * N < (int64_t)INT32_MAX;
+  const bool small = !c->index64 && (int64_t)Q * N < (int64_t)INT32_MAX;
+  const bool small15 = !c->index64 && (int64_t)15 * N < (int64_t)INT32_MAX;
   switch (stage) {
     case CACL_ADJ_CORRECT: {
       ACK(cudaMemcpyAsync(s->phib, in, pb, cudaMemcpyDeviceToDevice, st), "in");

@@ -646,6 +646,15 @@ cacl_status cacl_set_option(cacl_ctx* c, int option, int value) {
     c->phase_pipe = value;
     return CACL_OK;
   }
+  if (option == CACL_OPT_INDEX64) {
+    if (value != 0 && value != 1) return fail(c, CACL_ERR_ARG, "index64 is 0 or 1");
+    if (c->index64 != (value != 0)) {
+      drop_graphs(c);
+      c->index64 = value != 0;
+      CK(lb_init(c), "collide-stream setup");
+    }
+    return CACL_OK;
+  }
   return fail(c, CACL_ERR_ARG, "unknown option");
 }
 

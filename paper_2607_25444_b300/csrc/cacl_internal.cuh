@@ -420,6 +420,8 @@ struct cacl_ctx {
                            // staged rows, 2 one node per thread, 3 TMA-tiled
                            // (else two nodes per thread)
   int lb_grid = 1;         // blocks of the persistent staged collide-stream
+  bool index64 = false;    // 64-bit offsets in every kernel that has both
+                           // widths, whatever the size (CACL_OPT_INDEX64)
   // tensor maps of the TMA-tiled collide-stream (nx a multiple of 8):
   // population loads and stores per buffer, phi loads per buffer, u and a
   // stores; valid when lbt_ok

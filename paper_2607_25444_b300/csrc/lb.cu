@@ -1523,15 +1523,15 @@ lb_collide_batch(const CaseDesc* __restrict__ cases, WorkList wl, int fc,
 int staged_segments(const Grid& g) { return ((g.nx + SEG - 1) / SEG) * g.ny * g.nz; }
 
 template <typename Store>
-void* staged_kernel(const Grid& g) {
-  return ((int64_t)Q * g.N < (int64_t)INT32_MAX)
+void* staged_kernel(const Grid& g, bool index64) {
+  return (!index64 && (int64_t)Q * g.N < (int64_t)INT32_MAX)
              ? (void*)lb_collide_staged<Store, int>
              : (void*)lb_collide_staged<Store, int64_t>;
 }
 
 template <typename Store>
-cudaError_t staged_setup(const Grid& g, int* grid) {
-  void* fn = staged_kernel<Store>(g);
+cudaError_t staged_setup(const Grid& g, bool index64, int* grid) {
+  void* fn = staged_kernel<Store>(g, index64);
   const size_t smem = 2 * sizeof(StagedRows<Store>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -1612,7 +1612,7 @@ void launch_store(cacl_ctx* c, const void* fin, void* fout, const float* phi) {
   const Grid g = c->g;
   if (lb_staged_ok(c, fin, fout, phi)) {
     const int nseg = staged_segments(g);
-    void* fn = staged_kernel<Store>(g);
+    void* fn = staged_kernel<Store>(g, c->index64);
     const size_t smem = 2 * sizeof(StagedRows<Store>);
     const int grid = c->lb_grid;
     const T* fi = (const T*)fin;
@@ -1665,7 +1665,7 @@ void launch_store(cacl_ctx* c, const void* fin, void* fout, const float* phi) {
   }
   dim3 block(LB_BX, LB_BY, 1);
   dim3 grid((g.nx + LB_BX - 1) / LB_BX, (g.ny + LB_BY - 1) / LB_BY, g.nz);
-  if ((int64_t)Q * g.N < (int64_t)INT32_MAX)
+  if (!c->index64 && (int64_t)Q * g.N < (int64_t)INT32_MAX)
     lb_collide<Store, int><<<grid, block, 0, c->stream>>>(
         (const T*)fin, (T*)fout, phi, c->u, c->a, c->flags, g, c->k);
   else
@@ -1676,16 +1676,17 @@ void launch_store(cacl_ctx* c, const void* fin, void* fout, const float* phi) {
 }  // namespace
 
 // Resident-sized grid of the persistent copy-staged collide-stream (and its
-// shared-memory attribute), set once per context outside any graph capture.
+// shared-memory attribute), set per context (again when the offset width
+// changes) outside any graph capture.
 cudaError_t lb_init(cacl_ctx* c) {
   if (c->p.storage == CACL_F32_MOMENTS)
     return cudaFuncSetAttribute(lb_collide_moments,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(MomentSmem));
   switch (c->p.storage) {
-    case CACL_F16_SHIFTED: return staged_setup<StoreF16>(c->g, &c->lb_grid);
-    case CACL_BF16_SHIFTED: return staged_setup<StoreBF16>(c->g, &c->lb_grid);
-    default: return staged_setup<StoreF32>(c->g, &c->lb_grid);
+    case CACL_F16_SHIFTED: return staged_setup<StoreF16>(c->g, c->index64, &c->lb_grid);
+    case CACL_BF16_SHIFTED: return staged_setup<StoreBF16>(c->g, c->index64, &c->lb_grid);
+    default: return staged_setup<StoreF32>(c->g, c->index64, &c->lb_grid);
   }
 }
 
@@ -1702,12 +1703,13 @@ cudaError_t lb_tma_init(cacl_ctx* c) {
 
 // The TMA-tiled collide-stream (CACL_OPT_LB_PIPE = 3) runs on the
 // context's own population, phi, u and a buffers when nx is a multiple of 8
-// and 27 N < 2^31; otherwise the two-node kernel runs.
+// and 27 N < 2^31 (and 64-bit offsets are not forced); otherwise the
+// two-node kernel runs.
 bool lb_tma_ok(const cacl_ctx* c, const void* fin, const void* fout,
                const void* phi) {
   const bool fpair = (fin == c->f[0] && fout == c->f[1]) ||
                      (fin == c->f[1] && fout == c->f[0]);
-  return c->lb_pipe == 3 && c->lbt_ok && fpair &&
+  return c->lb_pipe == 3 && c->lbt_ok && !c->index64 && fpair &&
          (phi == c->phi[0] || phi == c->phi[1]);
 }
 
@@ -1723,26 +1725,27 @@ bool lb_staged_ok(const cacl_ctx* c, const void* fin, const void* fout,
 }
 
 // The two-node collide-stream (the default, CACL_OPT_LB_PIPE = 0, and the
-// fallback of 3) needs nx even, 27 N below 2^31 (32-bit offsets) and buffers
-// aligned for the pair accesses; otherwise, or with CACL_OPT_LB_PIPE = 2,
-// one node per thread.
+// fallback of 3) needs nx even, 27 N below 2^31 (32-bit offsets, not
+// forced to 64) and buffers aligned for the pair accesses; otherwise, or
+// with CACL_OPT_LB_PIPE = 2, one node per thread.
 bool lb_pair_ok(const cacl_ctx* c, const void* fin, const void* fout,
                 const void* phi) {
   const uintptr_t fa = 2 * storage_bytes(c->p.storage) - 1;
   auto al = [](const void* p, uintptr_t m) { return ((uintptr_t)p & m) == 0; };
-  return (c->lb_pipe == 0 || c->lb_pipe == 3) && c->g.nx % 2 == 0 &&
+  return (c->lb_pipe == 0 || c->lb_pipe == 3) && c->g.nx % 2 == 0 && !c->index64 &&
          (int64_t)Q * c->g.N < (int64_t)INT32_MAX && al(fin, fa) && al(fout, fa) &&
          al(phi, 7) && al(c->u, 7) && al(c->a, 7);
 }
 
 // The four-node collide-stream (16-bit populations, the default there)
-// needs nx a multiple of 4, 27 N below 2^31 and 8-byte aligned population
+// needs nx a multiple of 4, 27 N below 2^31 (offsets not forced to 64 bits)
+// and 8-byte aligned population
 // and 16-byte aligned phi, u, a buffers; otherwise the two-node kernel.
 bool lb_quad_ok(const cacl_ctx* c, const void* fin, const void* fout,
                 const void* phi) {
   auto al = [](const void* p, uintptr_t m) { return ((uintptr_t)p & m) == 0; };
   return c->lb_pipe == 0 && storage_bytes(c->p.storage) == 2 && c->g.nx % 4 == 0 &&
-         (int64_t)Q * c->g.N < (int64_t)INT32_MAX && al(fin, 7) && al(fout, 7) &&
+         !c->index64 && (int64_t)Q * c->g.N < (int64_t)INT32_MAX && al(fin, 7) && al(fout, 7) &&
          al(phi, 15) && al(c->u, 15) && al(c->a, 15);
 }
 
