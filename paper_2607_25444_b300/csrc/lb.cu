@@ -876,12 +876,12 @@ __device__ __forceinline__ void lb_quad(int x0, int y, int z,
   float2 axA, ayA, azA;
   compressive(phiA, gxA, gyA, gzA, axA, ayA, azA);
   float2 uxA, uyA, uzA;
+  T2 eA[Q];  // pair A's encoded f*, stored with pair B's as one 8-byte word
   {
     NodeOut<float2> o;
     collide(fA, phiA, gxA, gyA, gzA, lap_from_sum(phiA, ssA), k, o);
 #pragma unroll
-    for (int q = 0; q < Q; ++q)
-      *reinterpret_cast<T2*>(fout + q * N + n) = Store::encode_w2(o.P[q], q);
+    for (int q = 0; q < Q; ++q) eA[q] = Store::encode_w2(o.P[q], q);
     uxA = o.ux;
     uyA = o.uy;
     uzA = o.uz;
@@ -898,8 +898,13 @@ __device__ __forceinline__ void lb_quad(int x0, int y, int z,
     NodeOut<float2> o;
     collide(fB, phiB, gxB, gyB, gzB, lap_from_sum(phiB, ssB), k, o);
 #pragma unroll
-    for (int q = 0; q < Q; ++q)
-      *reinterpret_cast<T2*>(fout + q * N + n + 2) = Store::encode_w2(o.P[q], q);
+    for (int q = 0; q < Q; ++q) {
+      const T2 eB = Store::encode_w2(o.P[q], q);
+      uint2 w;
+      w.x = *reinterpret_cast<const uint32_t*>(&eA[q]);
+      w.y = *reinterpret_cast<const uint32_t*>(&eB);
+      *reinterpret_cast<uint2*>(fout + q * N + n) = w;
+    }
     *reinterpret_cast<float4*>(u + n) = make_float4(uxA.x, uxA.y, o.ux.x, o.ux.y);
     *reinterpret_cast<float4*>(u + N + n) = make_float4(uyA.x, uyA.y, o.uy.x, o.uy.y);
     *reinterpret_cast<float4*>(u + 2 * N + n) = make_float4(uzA.x, uzA.y, o.uz.x, o.uz.y);
@@ -908,13 +913,15 @@ __device__ __forceinline__ void lb_quad(int x0, int y, int z,
 
 // Block (LBQ_PX, LBQ_PY): 4 LBQ_PX nodes of LBQ_PY rows. A quad with a solid
 // node or a wall neighbour runs the one-node path on each node. Bounded to
-// 128 registers (four blocks per SM; ptxas spills 52 bytes): 0.512 ms per
-// 256^3 launch against 0.530 ms at 168 registers and 0.635 ms unbounded
-// (255 registers).
+// 128 registers (eight blocks of 64 threads per SM; ptxas spills about 70
+// bytes). FP16 at 256^3: 0.474 ms per launch; 0.479 with four blocks of 128
+// threads, 0.474 at 168 registers (BF16 0.513 there, 0.480 here), 0.511
+// when each pair's populations were stored as soon as the pair was done
+// (4-byte stores) rather than together (8-byte stores).
 constexpr int LBQ_PX = 32;
-constexpr int LBQ_PY = 4;
+constexpr int LBQ_PY = 2;
 template <typename Store>
-__global__ void __launch_bounds__(LBQ_PX * LBQ_PY, 4)
+__global__ void __launch_bounds__(LBQ_PX * LBQ_PY, 8)
 lb_collide_quad(const typename Store::T* __restrict__ fin,
                 typename Store::T* __restrict__ fout, const float* __restrict__ phi,
                 float* __restrict__ u, float* __restrict__ a,

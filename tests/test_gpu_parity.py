@@ -453,14 +453,16 @@ def _lb_pipes_agree(p, solid, phi, u, pipes, steps=20):
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("shape", [(64, 10, 9), (130, 6, 8), (2, 5, 6), (36, 12, 10),
-                                   (136, 6, 8), (16, 12, 10), (256, 4, 5)])
+                                   (136, 6, 8), (16, 12, 10), (256, 4, 5), (68, 7, 5)])
 def test_lb_kernels_bit_identical(storage, shape):
     """Two nodes per thread with packed pair arithmetic (the default), one
     node per thread, and the TMA-tiled form (where nx is a multiple of 8)
     give bit for bit the same populations, u, p* and phi over 20 full steps: one tile row narrower than a tile (nx = 64, 16), two tiles with
     both x edges (256), a partial last tile (136), a partial last block with
     the x wrap inside it for the pair kernel (nx = 130), a row that is a
-    single pair (both neighbours wrap onto the row itself) and a small box."""
+    single pair (both neighbours wrap onto the row itself), a small box and
+    an odd number of rows (a partial last block in y for the four-node
+    kernel)."""
     nx, ny, nz = shape
     p, solid, phi = _droplet_case(nx=nx, ny=ny, nz=nz, theta=70.0)
     p = dict(p, storage=storage, rho_g=0.3, nu_g=0.08)
