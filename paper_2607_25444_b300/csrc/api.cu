@@ -51,6 +51,8 @@ cudaError_t enqueue_step(cacl_ctx* c, int fc, int pc) {
   if ((e = launch_lb(c, c->f[fc], c->f[1 - fc], c->phi[pc])) != cudaSuccess)
     return e;
   if ((e = launch_phase(c, c->phi[pc], c->phi[1 - pc])) != cudaSuccess) return e;
+  if (c->zbase == 0 && c->zlim == 0 && !c->ext_finalize)
+    return launch_correct_tiles(c, c->phi[1 - pc]);
   return launch_correct(c, c->phi[1 - pc]);
 }
 

@@ -485,6 +485,9 @@ cudaError_t launch_compressive(cacl_ctx* c, const float* phi);
 cudaError_t phase_init_attributes();
 cudaError_t launch_phase(cacl_ctx* c, const float* phi_in, float* phi_out);
 cudaError_t launch_correct(cacl_ctx* c, float* phi);
+// the correction right after launch_phase over the whole context (tiles
+// without interface-band nodes skipped)
+cudaError_t launch_correct_tiles(cacl_ctx* c, float* phi);
 cudaError_t launch_mass_from(cacl_ctx* c, const double* partials, int nb);
 cudaError_t launch_mass_ref(cacl_ctx* c, const float* phi);
 cudaError_t launch_init_populations(cacl_ctx* c);

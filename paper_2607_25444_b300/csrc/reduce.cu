@@ -77,6 +77,40 @@ correct_phi(float* __restrict__ phi, const uint8_t* __restrict__ flags,
   correct_group(phi, flags, ms->lambda_f, ms->step, eps, N, i4, node_offset);
 }
 
+// The correction right after a phi update, tile by tile: block pb covers
+// the update's tile pb (32 x ty x zc nodes from (32 bx, ty by, zc bz)). chi
+// is non-negative, so a tile's chi sum, which the update left in wsum[pb],
+// is zero only when no node of the tile is in the interface band; there
+// phi = phi* and the block returns at once. Elsewhere the nodes are
+// corrected as in correct_phi (four per group when VEC, nx % 4 == 0), with
+// the same rounding keys, so the field is bit-identical to correct_phi's.
+template <bool VEC>
+__global__ void __launch_bounds__(ELEM_THREADS)
+correct_tiles(float* __restrict__ phi, const uint8_t* __restrict__ flags,
+              const MassScalars* __restrict__ ms, const double* __restrict__ wsum,
+              Grid g, int ty, int zc, float eps, int64_t node_offset) {
+  const int pb = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  if (!(wsum[pb] > 0.0)) return;
+  const float lam = ms->lambda_f;
+  const uint32_t step = ms->step;
+  const int x0 = 32 * blockIdx.x, y0 = ty * blockIdx.y, z0 = zc * blockIdx.z;
+  constexpr int PER_ROW = VEC ? 8 : 32;  // groups (or nodes) per tile row
+  const int items = ty * zc * PER_ROW;
+  for (int j = threadIdx.x; j < items; j += ELEM_THREADS) {
+    const int r = j / PER_ROW, c = j % PER_ROW;
+    const int x = x0 + (VEC ? 4 * c : c), y = y0 + r % ty, z = z0 + r / ty;
+    if (x >= g.nx || y >= g.ny || z >= g.nz) continue;
+    const int64_t n = x + (int64_t)g.nx * (y + (int64_t)g.ny * z);
+    if (VEC) {
+      correct_group(phi, flags, lam, step, eps, g.N, n, node_offset);
+    } else {
+      const float s = phi[n];
+      if ((s > eps && s < 1.0f - eps) && !(flags[n] & FLAG_SOLID))
+        phi[n] = add_unbiased(s, lam * (s * (1.0f - s)), step, node_offset + n);
+    }
+  }
+}
+
 // Batched correction: virtual block b covers 4 * ELEM_THREADS nodes of its
 // case, four per thread as in correct_phi.
 __global__ void __launch_bounds__(ELEM_THREADS)
@@ -199,6 +233,22 @@ cudaError_t launch_correct(cacl_ctx* c, float* phi) {
   const int nb = (int)((N + 4 * ELEM_THREADS - 1) / (4 * ELEM_THREADS));
   correct_phi<<<nb, ELEM_THREADS, 0, c->stream>>>(phi, c->flags, c->mass, N,
                                                  c->k.eps_phi, c->node_offset);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_correct_tiles(cacl_ctx* c, float* phi) {
+  // the tiles and chi sums of the phi update that wrote phi
+  int ty = 0, zc = 0;
+  phase_tile(c->phase_variant, ty, zc);
+  const Grid g = c->g;
+  const dim3 grid((g.nx + 31) / 32, (g.ny + ty - 1) / ty, (g.nz + zc - 1) / zc);
+  const double* wsum = c->partials + c->phase_nblocks;
+  if (g.nx % 4 == 0 && ((uintptr_t)phi & 15u) == 0)
+    correct_tiles<true><<<grid, ELEM_THREADS, 0, c->stream>>>(
+        phi, c->flags, c->mass, wsum, g, ty, zc, c->k.eps_phi, c->node_offset);
+  else
+    correct_tiles<false><<<grid, ELEM_THREADS, 0, c->stream>>>(
+        phi, c->flags, c->mass, wsum, g, ty, zc, c->k.eps_phi, c->node_offset);
   return cudaGetLastError();
 }
 
