@@ -182,7 +182,10 @@ cacl_status cacl_load_state(cacl_ctx* ctx, const void* host_buf, int64_t bytes);
 cacl_status cacl_inject_wait_timeout(cacl_ctx* ctx);
 
 /* Advance nsteps >= 0 full steps (ghost update, collide-stream, phi update,
- * volume correction) on the context stream; does not synchronise. */
+ * volume correction) on the context stream; does not synchronise. The
+ * step's correction visits only the phi-update tiles whose chi sum is
+ * positive (chi >= 0, so the others hold no interface-band node and keep
+ * phi = phi*); the result is bit-identical to correcting every node. */
 cacl_status cacl_step(cacl_ctx* ctx, int nsteps);
 
 /* The four parts of one step, enqueued singly (for inspection and part by
