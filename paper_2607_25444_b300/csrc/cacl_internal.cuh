@@ -136,9 +136,16 @@ __device__ __forceinline__ int wrap(int i, int d, int n) {
 
 // Arithmetic on one node (float) or on a pair of x-adjacent nodes (float2,
 // the packed FP32 pair operations of sm_100 and later). Every operation is
-// round-to-nearest and is never contracted, and a pair operation rounds
-// each lane exactly as the scalar operation does, so a kernel that handles
-// two nodes per thread gives the same bits as one that handles one.
+// round-to-nearest, and a pair operation rounds each lane exactly as the
+// scalar operation does, so a kernel that handles two nodes per thread
+// gives the same bits as one that handles one. The scalar forms are never
+// contracted; a packed product that feeds a packed sum directly is fused
+// into one packed multiply-add by this toolchain (CUDA 13.0) even with
+// explicit rounding (measured: __fadd2_rn(__fmul2_rn(a, b), c) equals
+// fmaf lane by lane, and differs from the two rounded scalar operations in
+// 14% of random lanes), so pair code keeps such a product apart from its sum
+// (a select, or a use as an addend of vfma), and the pair kernels are
+// checked bit for bit against the one-node kernels.
 __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
   return __ffma2_rn(a, b, c);
