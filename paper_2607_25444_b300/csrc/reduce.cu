@@ -36,9 +36,28 @@ finalize_mass_batch(const CaseDesc* __restrict__ cases) {
   mass_from_partials(cd.partials, cd.phase_nb, cd.mass, threadIdx.x);
 }
 
-// phi = phi* + lambda chi(phi*) at the fluid nodes i4 .. i4 + 3 of a field
-// of N nodes (i4 a multiple of 4), rounded without bias; the rounding key of
-// node n is node_offset + n.
+// phi = phi* + lambda chi(phi*) at the fluid nodes of a group of four
+// held in registers (v, their flags fl), rounded without bias; the rounding
+// key of the group's first node is key0. Returns whether any node of the
+// group is in the interface band (outside it chi = 0 and phi is unchanged).
+__device__ __forceinline__ bool correct4(float4& v, uchar4 fl, float lam, uint32_t step,
+                                         float eps, int64_t key0) {
+  float* pv = &v.x;
+  const uint8_t fa[4] = {fl.x, fl.y, fl.z, fl.w};
+  bool band = false;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float s = pv[j];
+    const bool in = (s > eps && s < 1.0f - eps) && !(fa[j] & FLAG_SOLID);
+    if (in) pv[j] = add_unbiased(s, lam * (s * (1.0f - s)), step, key0 + j);
+    band |= in;
+  }
+  return band;
+}
+
+// The same at the fluid nodes i4 .. i4 + 3 of a field of N nodes (i4 a
+// multiple of 4, fewer at the end); the rounding key of node n is
+// node_offset + n.
 __device__ __forceinline__ void correct_group(float* __restrict__ phi,
                                               const uint8_t* __restrict__ flags,
                                               float lam, uint32_t step, float eps,
@@ -47,18 +66,8 @@ __device__ __forceinline__ void correct_group(float* __restrict__ phi,
   if (i4 + 3 < N) {
     float4 v = *reinterpret_cast<const float4*>(phi + i4);
     const uchar4 fl = *reinterpret_cast<const uchar4*>(flags + i4);
-    float* pv = &v.x;
-    const uint8_t fa[4] = {fl.x, fl.y, fl.z, fl.w};
-    bool band = false;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float s = pv[j];
-      const bool in = (s > eps && s < 1.0f - eps) && !(fa[j] & FLAG_SOLID);
-      if (in) pv[j] = add_unbiased(s, lam * (s * (1.0f - s)), step, node_offset + i4 + j);
-      band |= in;
-    }
-    // outside the interface band chi = 0 and phi is unchanged: no store
-    if (band) *reinterpret_cast<float4*>(phi + i4) = v;
+    if (correct4(v, fl, lam, step, eps, node_offset + i4))
+      *reinterpret_cast<float4*>(phi + i4) = v;  // band nodes only
   } else {
     for (int64_t n = i4; n < N; ++n) {
       const float s = phi[n];
@@ -77,36 +86,71 @@ correct_phi(float* __restrict__ phi, const uint8_t* __restrict__ flags,
   correct_group(phi, flags, ms->lambda_f, ms->step, eps, N, i4, node_offset);
 }
 
-// The correction right after a phi update, tile by tile: block pb covers
-// the update's tile pb (32 x ty x zc nodes from (32 bx, ty by, zc bz)). chi
-// is non-negative, so a tile's chi sum, which the update left in wsum[pb],
-// is zero only when no node of the tile is in the interface band; there
-// phi = phi* and the block returns at once. Elsewhere the nodes are
+// The correction right after a phi update, by the update's tiles (32 x ty x
+// zc nodes from (32 bx, ty by, zc bz); ty, zc powers of two). chi is
+// non-negative, so a tile's chi sum, which the update left in wsum, is zero
+// only when no node of the tile is in the interface band; there phi = phi*
+// is left as it is. A tile is split along z into `split` blocks (block
+// (bx, by, bz') covers planes zc bz + tz s .. + tz - 1 of tile (bx, by, bz),
+// tz = zc / split, s = bz' % split): many tiles take one block each, and
+// the few tiles of a small grid spread their band work over several; a
+// block of a tile without band nodes returns after one load. The nodes are
 // corrected as in correct_phi (four per group when VEC, nx % 4 == 0), with
-// the same rounding keys, so the field is bit-identical to correct_phi's.
-template <bool VEC>
+// the same rounding keys: the field is bit-identical to correct_phi's. A
+// thread loads up to TB groups before it corrects and stores them.
+template <bool VEC, int TB>
 __global__ void __launch_bounds__(ELEM_THREADS)
 correct_tiles(float* __restrict__ phi, const uint8_t* __restrict__ flags,
               const MassScalars* __restrict__ ms, const double* __restrict__ wsum,
-              Grid g, int ty, int zc, float eps, int64_t node_offset) {
-  const int pb = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+              Grid g, int ty, int zc, int split, float eps, int64_t node_offset) {
+  const int bz = blockIdx.z / split, sz = blockIdx.z % split;
+  const int pb = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * bz);
   if (!(wsum[pb] > 0.0)) return;
   const float lam = ms->lambda_f;
   const uint32_t step = ms->step;
-  const int x0 = 32 * blockIdx.x, y0 = ty * blockIdx.y, z0 = zc * blockIdx.z;
+  const int tz = zc / split;
+  const int x0 = 32 * blockIdx.x, y0 = ty * blockIdx.y, z0 = zc * bz + tz * sz;
   constexpr int PER_ROW = VEC ? 8 : 32;  // groups (or nodes) per tile row
-  const int items = ty * zc * PER_ROW;
-  for (int j = threadIdx.x; j < items; j += ELEM_THREADS) {
-    const int r = j / PER_ROW, c = j % PER_ROW;
-    const int x = x0 + (VEC ? 4 * c : c), y = y0 + r % ty, z = z0 + r / ty;
-    if (x >= g.nx || y >= g.ny || z >= g.nz) continue;
-    const int64_t n = x + (int64_t)g.nx * (y + (int64_t)g.ny * z);
-    if (VEC) {
-      correct_group(phi, flags, lam, step, eps, g.N, n, node_offset);
+  const int items = ty * tz * PER_ROW;
+  for (int j0 = threadIdx.x; j0 < items; j0 += TB * ELEM_THREADS) {
+    int64_t n[TB];
+    bool ok[TB];
+#pragma unroll
+    for (int t = 0; t < TB; ++t) {
+      const int j = j0 + t * ELEM_THREADS;
+      const int r = j / PER_ROW, c = j % PER_ROW;
+      const int x = x0 + (VEC ? 4 * c : c), y = y0 + r % ty, z = z0 + r / ty;
+      ok[t] = j < items && x < g.nx && y < g.ny && z < g.nz;
+      n[t] = x + (int64_t)g.nx * (y + (int64_t)g.ny * z);
+    }
+    if constexpr (VEC) {
+      float4 v[TB];
+      uchar4 fl[TB];
+#pragma unroll
+      for (int t = 0; t < TB; ++t)
+        if (ok[t]) {
+          v[t] = *reinterpret_cast<const float4*>(phi + n[t]);
+          fl[t] = *reinterpret_cast<const uchar4*>(flags + n[t]);
+        }
+#pragma unroll
+      for (int t = 0; t < TB; ++t)
+        if (ok[t] && correct4(v[t], fl[t], lam, step, eps, node_offset + n[t]))
+          *reinterpret_cast<float4*>(phi + n[t]) = v[t];
     } else {
-      const float s = phi[n];
-      if ((s > eps && s < 1.0f - eps) && !(flags[n] & FLAG_SOLID))
-        phi[n] = add_unbiased(s, lam * (s * (1.0f - s)), step, node_offset + n);
+      float v[TB];
+      uint8_t fl[TB];
+#pragma unroll
+      for (int t = 0; t < TB; ++t)
+        if (ok[t]) {
+          v[t] = phi[n[t]];
+          fl[t] = flags[n[t]];
+        }
+#pragma unroll
+      for (int t = 0; t < TB; ++t) {
+        const float s = v[t];
+        if (ok[t] && (s > eps && s < 1.0f - eps) && !(fl[t] & FLAG_SOLID))
+          phi[n[t]] = add_unbiased(s, lam * (s * (1.0f - s)), step, node_offset + n[t]);
+      }
     }
   }
 }
@@ -241,14 +285,18 @@ cudaError_t launch_correct_tiles(cacl_ctx* c, float* phi) {
   int ty = 0, zc = 0;
   phase_tile(c->phase_variant, ty, zc);
   const Grid g = c->g;
-  const dim3 grid((g.nx + 31) / 32, (g.ny + ty - 1) / ty, (g.nz + zc - 1) / zc);
+  const int gx = (g.nx + 31) / 32, gy = (g.ny + ty - 1) / ty, gz = (g.nz + zc - 1) / zc;
+  // at least about 2048 blocks (the tiles of 256^3), at most 4 planes each
+  int split = 1;
+  while (split < zc / 4 && (int64_t)gx * gy * gz * split < 2048) split *= 2;
+  const dim3 grid(gx, gy, gz * split);
   const double* wsum = c->partials + c->phase_nblocks;
-  if (g.nx % 4 == 0 && ((uintptr_t)phi & 15u) == 0)
-    correct_tiles<true><<<grid, ELEM_THREADS, 0, c->stream>>>(
-        phi, c->flags, c->mass, wsum, g, ty, zc, c->k.eps_phi, c->node_offset);
-  else
-    correct_tiles<false><<<grid, ELEM_THREADS, 0, c->stream>>>(
-        phi, c->flags, c->mass, wsum, g, ty, zc, c->k.eps_phi, c->node_offset);
+  const bool vec = g.nx % 4 == 0 && ((uintptr_t)phi & 15u) == 0;
+  // groups in flight per thread: all of a whole tile's share, or two
+  auto fn = vec ? (split == 1 ? correct_tiles<true, 8> : correct_tiles<true, 2>)
+                : (split == 1 ? correct_tiles<false, 8> : correct_tiles<false, 2>);
+  fn<<<grid, ELEM_THREADS, 0, c->stream>>>(phi, c->flags, c->mass, wsum, g, ty, zc, split,
+                                           c->k.eps_phi, c->node_offset);
   return cudaGetLastError();
 }
 
