@@ -341,10 +341,12 @@ cacl_status cacl_batch_autotune(cacl_batch* batch, int steps, int* lb_variant,
  * 3 = 32x16 x 32. CACL_OPT_PHASE_PIPE selects how the phase update stages
  * its planes in shared memory and how many nodes a thread evaluates:
  * 0 = automatic (3 when nx is a multiple of 4, nz >= 2 and the fields are
- * 16-byte aligned, else 1), 1 = staging through registers, 2 = asynchronous
- * 16-byte copies, two nodes per thread along y, 3 = asynchronous copies,
- * 2 x 2 nodes per thread (an x pair on two rows, packed pair arithmetic);
- * 2 and 3 return CACL_ERR_ARG when nx is not a multiple of 4 or nz < 2. All
+ * 16-byte aligned; else 2 when nz >= 2; else 1), 1 = staging through
+ * registers, 2 = asynchronous copies (16-byte copies when nx is a multiple
+ * of 4, else 4-byte copies element by element), two nodes per thread along
+ * y, 3 = asynchronous 16-byte copies, 2 x 2 nodes per thread (an x pair on
+ * two rows, packed pair arithmetic); 2 returns CACL_ERR_ARG when nz < 2, 3
+ * also when nx is not a multiple of 4. All
  * give bit-identical phi*; the partial sums of the volume correction agree
  * to the rounding of their summation order, bit for bit between 1 and 2.
  * CACL_OPT_LB_PIPE selects how the collide-stream

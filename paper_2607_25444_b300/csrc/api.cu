@@ -642,8 +642,10 @@ cacl_status cacl_set_option(cacl_ctx* c, int option, int value) {
   }
   if (option == CACL_OPT_PHASE_PIPE) {
     if (value < 0 || value > 3) return fail(c, CACL_ERR_ARG, "unknown phase pipeline");
-    if (value >= 2 && (c->g.nx % 4 != 0 || c->g.nz < 2))
-      return fail(c, CACL_ERR_ARG, "copy-staged phase update needs nx % 4 == 0, nz >= 2");
+    if (value >= 2 && c->g.nz < 2)
+      return fail(c, CACL_ERR_ARG, "copy-staged phase update needs nz >= 2");
+    if (value == 3 && c->g.nx % 4 != 0)
+      return fail(c, CACL_ERR_ARG, "2 x 2 phase update needs nx % 4 == 0");
     if (c->phase_pipe != value) drop_graphs(c);
     c->phase_pipe = value;
     return CACL_OK;

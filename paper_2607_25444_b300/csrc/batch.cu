@@ -26,12 +26,13 @@ struct cacl_batch {
   int* d_starts = nullptr;  // NLISTS lists of ncases + 1 starts
   // collide-stream: the cases of one, two and four nodes per thread
   // (wl_lb[w], w = 0, 1, 2); phi update: the cases of width class w staged
-  // through registers (wl_ph[0][w]), by copies with two nodes per thread
-  // (wl_ph[1][w]) and with 2 x 2 (wl_ph[2][w]); each as the case would run
+  // through registers (wl_ph[0][w]), by 16-byte copies with two nodes per
+  // thread (wl_ph[1][w]), with 2 x 2 (wl_ph[2][w]) and by element copies
+  // with two nodes per thread (wl_ph[3][w]); each as the case would run
   // alone
-  WorkList wl_lb[3]{}, wl_ph[3][3]{}, wl_ghost{}, wl_corr{};
+  WorkList wl_lb[3]{}, wl_ph[4][3]{}, wl_ghost{}, wl_corr{};
   int grid_lb[3] = {0, 0, 0};
-  int grid_ph[3][3] = {};
+  int grid_ph[4][3] = {};
   int grid_ghost = 0, grid_corr = 0;
   // the width classes touch disjoint cases: in the captured step each runs
   // its collide-stream and phi update as a branch of its own (side streams
@@ -47,7 +48,7 @@ struct cacl_batch {
 
 namespace {
 
-constexpr int NLISTS = 14;  // ghost, correction, 3 collide-stream, 3 x 3 phi
+constexpr int NLISTS = 17;  // ghost, correction, 3 collide-stream, 4 x 3 phi
 constexpr int LB_WIDTH[3] = {1, 2, 4};
 
 cacl_status bfail(cacl_batch* b, cacl_status st, const std::string& msg) {
@@ -88,8 +89,8 @@ cacl_status build_plan(cacl_batch* b) {
   int* s_gh = list(0);
   int* s_cr = list(1);
   int* s_lb[3] = {list(2), list(3), list(4)};
-  int* s_ph[3][3];
-  for (int q = 0; q < 3; ++q)
+  int* s_ph[4][3];
+  for (int q = 0; q < 4; ++q)
     for (int w = 0; w < 3; ++w) s_ph[q][w] = list(5 + 3 * q + w);
   const int row = lb_batch_row(b->lb_variant);
   int ty = 16, zc = 16;
@@ -137,8 +138,9 @@ cacl_status build_plan(cacl_batch* b) {
     }
     const bool copy = c->phase_pipe != 1 &&
                       phase_copy_ok(c->g, c->phi[0], c->phi[1], c->a, c->u, c->flags);
-    const int pipe = !copy ? 0 : (c->phase_pipe == 2 ? 1 : 2);
-    for (int q = 0; q < 3; ++q)
+    const bool copy_u = c->phase_pipe != 1 && !copy && c->g.nz >= 2;
+    const int pipe = copy_u ? 3 : (!copy ? 0 : (c->phase_pipe == 2 ? 1 : 2));
+    for (int q = 0; q < 4; ++q)
       for (int w = 0; w < 3; ++w)
         s_ph[q][w][i + 1] = s_ph[q][w][i] + (q == pipe && w == wc ? d.phase_nb : 0);
     s_gh[i + 1] = s_gh[i] + (c->wall_count + ghost_batch_block() - 1) /
@@ -155,7 +157,7 @@ cacl_status build_plan(cacl_batch* b) {
   b->wl_ghost = {dlist(0), nc, s_gh[nc]};
   b->wl_corr = {dlist(1), nc, s_cr[nc]};
   for (int w = 0; w < 3; ++w) b->wl_lb[w] = {dlist(2 + w), nc, s_lb[w][nc]};
-  for (int q = 0; q < 3; ++q)
+  for (int q = 0; q < 4; ++q)
     for (int w = 0; w < 3; ++w)
       b->wl_ph[q][w] = {dlist(5 + 3 * q + w), nc, s_ph[q][w][nc]};
   // persistent grids: as many blocks as stay resident, at most the work
@@ -172,10 +174,11 @@ cacl_status build_plan(cacl_batch* b) {
                    ? grid_for(b->wl_lb[w].total,
                               lb_batch_occupancy(b->storage, LB_WIDTH[w], b->lb_variant))
                    : b->wl_lb[w].total);
-  const int occ[3] = {phase_batch_occupancy(b->phase_variant),
-                      phase_batch_copy_occupancy(b->phase_variant),
-                      phase_batch_quad_occupancy(b->phase_variant)};
-  for (int q = 0; q < 3; ++q)
+  const int occ[4] = {phase_batch_occupancy(b->phase_variant),
+                      phase_batch_copy_occupancy(b->phase_variant, true),
+                      phase_batch_quad_occupancy(b->phase_variant),
+                      phase_batch_copy_occupancy(b->phase_variant, false)};
+  for (int q = 0; q < 4; ++q)
     for (int w = 0; w < 3; ++w) b->grid_ph[q][w] = grid_for(b->wl_ph[q][w].total, occ[q]);
   b->grid_ghost = grid_for(b->wl_ghost.total, 8);
   b->grid_corr = grid_for(b->wl_corr.total, 8);
@@ -183,12 +186,14 @@ cacl_status build_plan(cacl_batch* b) {
   return CACL_OK;
 }
 
-// phi-update launch of pipeline q (0 registers, 1 two-node copies, 2 2 x 2)
+// phi-update launch of pipeline q (0 registers, 1 two-node 16-byte copies,
+// 2 2 x 2, 3 two-node element copies)
 cudaError_t launch_phase_pipe(const CaseDesc* cases, WorkList wl, int q, int variant,
                               int grid, int pc, cudaStream_t st) {
   switch (q) {
     case 0: return launch_phase_batch(cases, wl, variant, grid, pc, st);
-    case 1: return launch_phase_batch_copy(cases, wl, variant, grid, pc, st);
+    case 1: return launch_phase_batch_copy(cases, wl, variant, grid, pc, true, st);
+    case 3: return launch_phase_batch_copy(cases, wl, variant, grid, pc, false, st);
     default: return launch_phase_batch_quad(cases, wl, variant, grid, pc, st);
   }
 }
@@ -213,7 +218,7 @@ cudaError_t enqueue_batch_step(cacl_batch* b, int par) {
     if ((e = launch_lb_batch(b->d_cases, b->wl_lb[w], b->storage, LB_WIDTH[w],
                              b->lb_variant, b->grid_lb[w], par, par, sw)) != cudaSuccess)
       return e;
-    for (int q = 0; q < 3; ++q)
+    for (int q = 0; q < 4; ++q)
       if (b->wl_ph[q][w].total > 0 &&
           (e = launch_phase_pipe(b->d_cases, b->wl_ph[q][w], q, b->phase_variant,
                                  b->grid_ph[q][w], par, sw)) != cudaSuccess)

@@ -529,8 +529,8 @@ int phase_batch_occupancy(int variant);
 // the same over cases that qualify for copy staging (phase_copy_ok): two
 // nodes per thread along y (phase pipeline 2) or 2 x 2 (0 and 3)
 cudaError_t launch_phase_batch_copy(const CaseDesc* cases, WorkList wl, int variant,
-                                    int grid, int pc, cudaStream_t st);
-int phase_batch_copy_occupancy(int variant);
+                                    int grid, int pc, bool aligned, cudaStream_t st);
+int phase_batch_copy_occupancy(int variant, bool aligned);
 cudaError_t launch_phase_batch_quad(const CaseDesc* cases, WorkList wl, int variant,
                                     int grid, int pc, cudaStream_t st);
 int phase_batch_quad_occupancy(int variant);

@@ -651,10 +651,15 @@ struct CopyTile {
 };
 
 // The same tile as phase_tile_body with every plane staged by cp.async
-// copies issued D planes ahead (no register staging, no shared-memory
-// stores by the threads). Requires nx % 4 == 0. smem is the dynamic shared
-// memory of CopyTile<TY, D>::bytes.
-template <int TY, int ZC, int D>
+// copies issued D planes ahead. AL (nx % 4 == 0, 16-byte aligned fields):
+// one 16-byte copy per 4-node chunk, the flags by 4-byte copies. Otherwise
+// (any nx): one 4-byte copy per element, consecutive threads on
+// consecutive elements of a window, each at its own wrapped column; the
+// flag bytes (whose rows are not 4-byte aligned) are loaded into registers
+// when their plane's copies are issued and stored into shared memory one
+// step later, before the barrier that publishes them. Requires nz >= 2.
+// smem is the dynamic shared memory of CopyTile<TY, D>::bytes.
+template <int TY, int ZC, int D, bool AL = true>
 __device__ __forceinline__ void phase_tile_copy(
     int bxi, int byi, int bzi, int pb, const float* __restrict__ phi,
     const float* __restrict__ afld, float* __restrict__ phi_out,
@@ -693,29 +698,93 @@ __device__ __forceinline__ void phase_tile_copy(
   const int gy = w8 + g.nx * mod(y0 - 1 + r8, g.ny), s8 = r8 * TX + 4 * c8;
   const int gz = w8 + g.nx * mod(y0 + r8, g.ny);       // slot offset s8
 
+  // element jobs (!AL): element j = tid + i THREADS of each window (the
+  // slot offset is j; consecutive threads copy consecutive elements), with
+  // its global in-plane offset (-1: none)
+  constexpr int WP = L::PR * CW, WA = L::AR * CW, WX = L::UX, WY = L::UY, WZ = L::UZ;
+  constexpr int NPE = AL ? 1 : (WP + THREADS - 1) / THREADS;
+  constexpr int NAE = AL ? 1 : (WA + THREADS - 1) / THREADS;
+  constexpr int NXE = AL ? 1 : (WX + THREADS - 1) / THREADS;
+  constexpr int NYE = AL ? 1 : (WY + THREADS - 1) / THREADS;
+  constexpr int NZE = AL ? 1 : (WZ + THREADS - 1) / THREADS;
+  int ope[NPE], oae[NAE], oxe[NXE], oye[NYE], oze[NZE];
+  uint8_t fpend[NPE];  // flag bytes waiting for their shared-memory store
+  int fslot = -1;      // ... and their slot (-1: none)
+  if constexpr (!AL) {
+    auto off40 = [&](int j, int w, int ylo) {  // 40-column window, rows from ylo
+      return j < w ? mod(x0 - 4 + j % CW, g.nx) + g.nx * mod(ylo + j / CW, g.ny) : -1;
+    };
+    auto off32 = [&](int j, int w, int ylo) {  // 32-column window
+      return j < w ? mod(x0 + j % TX, g.nx) + g.nx * mod(ylo + j / TX, g.ny) : -1;
+    };
+#pragma unroll
+    for (int i = 0; i < NPE; ++i) ope[i] = off40(tid + i * THREADS, WP, y0 - 2);
+#pragma unroll
+    for (int i = 0; i < NAE; ++i) oae[i] = off40(tid + i * THREADS, WA, y0 - 1);
+#pragma unroll
+    for (int i = 0; i < NXE; ++i) oxe[i] = off40(tid + i * THREADS, WX, y0);
+#pragma unroll
+    for (int i = 0; i < NYE; ++i) oye[i] = off32(tid + i * THREADS, WY, y0 - 1);
+#pragma unroll
+    for (int i = 0; i < NZE; ++i) oze[i] = off32(tid + i * THREADS, WZ, y0);
+  }
+  // a window's elements into shared memory (!AL)
+  auto elems = [&](float* dst, const float* plane, const int* off, int n) {
+#pragma unroll
+    for (int i = 0; i < n; ++i)
+      if (off[i] >= 0) cp_async4(dst + tid + i * THREADS, plane + off[i]);
+  };
+
   const int nb = zend - z0 + 2;  // bundles / steps: planes z0-2 .. zend-1
-  auto issue_phi = [&](int p, int slot) {  // phi and flags of plane p
+  // phi and flags of plane p; !AL with defer: the flag bytes are stored at
+  // the next step
+  auto issue_phi = [&](int p, int slot, bool defer) {
     const int64_t zo = (int64_t)wrap1(p, g.nz) * nxy;
-    if (hp) {
-      cp_async16(s_phi + slot * L::PHI + sp, phi + zo + gp);
-      cp_async4(s_flg + slot * L::FLG + sp, flags + zo + gp);
+    if constexpr (AL) {
+      if (hp) {
+        cp_async16(s_phi + slot * L::PHI + sp, phi + zo + gp);
+        cp_async4(s_flg + slot * L::FLG + sp, flags + zo + gp);
+      }
+    } else {
+      elems(s_phi + slot * L::PHI, phi + zo, ope, NPE);
+      uint8_t* sf = s_flg + slot * L::FLG;
+#pragma unroll
+      for (int i = 0; i < NPE; ++i) {
+        if (ope[i] < 0) continue;
+        const uint8_t f = __ldg(flags + zo + ope[i]);
+        if (defer)
+          fpend[i] = f;
+        else
+          sf[tid + i * THREADS] = f;
+      }
+      if (defer) fslot = slot;
     }
   };
-  auto issue = [&](int b) {  // bundle b: step kz = z0 - 2 + b
+  auto issue = [&](int b, bool defer) {  // bundle b: step kz = z0 - 2 + b
     const int t = z0 - 2 + b;
-    issue_phi(t + 2, (b + 2) & (L::RP - 1));
+    issue_phi(t + 2, (b + 2) & (L::RP - 1), defer);
     float* sa = s_au + (b & (L::RA - 1)) * L::ASLOT;
     const int64_t z1 = (int64_t)wrap1(t + 1, g.nz) * nxy;
-    if (ha) {
+    const int64_t z0o = (int64_t)wrap1(t, g.nz) * nxy;  // output plane t
+    if constexpr (AL) {
+      if (ha) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-        cp_async16(sa + c * L::AC + sp, afld + c * N + z1 + ga);
-    }
-    if (hz) cp_async16(sa + 3 * L::AC + L::UX + L::UY + s8, u + 2 * N + z1 + gz);
-    if (b >= 2) {  // output plane t
-      const int64_t z0o = (int64_t)wrap1(t, g.nz) * nxy;
-      if (hx) cp_async16(sa + 3 * L::AC + sp, u + z0o + gx);
-      if (hy) cp_async16(sa + 3 * L::AC + L::UX + s8, u + N + z0o + gy);
+        for (int c = 0; c < 3; ++c)
+          cp_async16(sa + c * L::AC + sp, afld + c * N + z1 + ga);
+      }
+      if (hz) cp_async16(sa + 3 * L::AC + L::UX + L::UY + s8, u + 2 * N + z1 + gz);
+      if (b >= 2) {
+        if (hx) cp_async16(sa + 3 * L::AC + sp, u + z0o + gx);
+        if (hy) cp_async16(sa + 3 * L::AC + L::UX + s8, u + N + z0o + gy);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) elems(sa + c * L::AC, afld + c * N + z1, oae, NAE);
+      elems(sa + 3 * L::AC + L::UX + L::UY, u + 2 * N + z1, oze, NZE);
+      if (b >= 2) {
+        elems(sa + 3 * L::AC, u + z0o, oxe, NXE);
+        elems(sa + 3 * L::AC + L::UX, u + N + z0o, oye, NYE);
+      }
     }
   };
 
@@ -733,20 +802,32 @@ __device__ __forceinline__ void phase_tile_copy(
   const int czu = tx + TX * (2 * ty);           // row a in the u_z window
 
   // prologue: phi planes z0-2, z0-1 with bundle 0, then bundles 1 .. D-1
-  issue_phi(z0 - 2, 0);
-  issue_phi(z0 - 1, 1);
-  issue(0);
+  // (their flag bytes stored at once: the first barrier publishes them)
+  issue_phi(z0 - 2, 0, false);
+  issue_phi(z0 - 1, 1, false);
+  issue(0, false);
   cp_async_commit();
 #pragma unroll
   for (int b = 1; b < D; ++b) {
-    if (b < nb) issue(b);
+    if (b < nb) issue(b, false);
     cp_async_commit();
   }
 
   March m;
   march_init(m);
   for (int b = 0; b < nb; ++b) {
-    if (b + D < nb) issue(b + D);
+    if constexpr (!AL) {
+      // the flag bytes loaded at the previous step: their slot was last read
+      // before that step's barrier, and is next read D - 1 steps from now
+      if (fslot >= 0) {
+        uint8_t* sf = s_flg + fslot * L::FLG;
+#pragma unroll
+        for (int i = 0; i < NPE; ++i)
+          if (ope[i] >= 0) sf[tid + i * THREADS] = fpend[i];
+      }
+      fslot = -1;
+    }
+    if (b + D < nb) issue(b + D, true);
     cp_async_commit();
     cp_async_wait<D>();
     __syncthreads();
@@ -1216,7 +1297,7 @@ phase_update_march(const float* __restrict__ phi, const float* __restrict__ afld
   finish_mass(partials, nblocks, ms, ticket, threadIdx.x + TX * threadIdx.y);
 }
 
-template <int TY, int ZC, int D, int MINB>
+template <int TY, int ZC, int D, int MINB, bool AL = true>
 __global__ void __launch_bounds__(TX * TY / 2, MINB)
 phase_update_copy(const float* __restrict__ phi, const float* __restrict__ afld,
                   float* __restrict__ phi_out, const float* __restrict__ u,
@@ -1225,9 +1306,9 @@ phase_update_copy(const float* __restrict__ phi, const float* __restrict__ afld,
                   Consts k, MassScalars* ms, unsigned* ticket, int zbase, int zlim) {
   extern __shared__ __align__(16) float dsm[];
   const int pb = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  phase_tile_copy<TY, ZC, D>(blockIdx.x, blockIdx.y, blockIdx.z, pb, phi, afld,
-                             phi_out, u, flags, partials, nblocks, g, k, dsm, zbase,
-                             zlim);
+  phase_tile_copy<TY, ZC, D, AL>(blockIdx.x, blockIdx.y, blockIdx.z, pb, phi, afld,
+                                 phi_out, u, flags, partials, nblocks, g, k, dsm, zbase,
+                                 zlim);
   finish_mass(partials, nblocks, ms, ticket, threadIdx.x + TX * threadIdx.y);
 }
 
@@ -1325,11 +1406,25 @@ CopyKernel copy_kernel(int variant) {
   }
 }
 
+// the same with element-wise staging (any nx)
+CopyKernel copy_kernel_u(int variant) {
+  switch (variant) {
+    case 1:
+      return {(void*)phase_update_copy<8, 16, COPY_D, 4, false>, CopyTile<8, COPY_D>::bytes};
+    case 2:
+      return {(void*)phase_update_copy<8, 32, COPY_D, 4, false>, CopyTile<8, COPY_D>::bytes};
+    case 3:
+      return {(void*)phase_update_copy<16, 32, COPY_D, 2, false>, CopyTile<16, COPY_D>::bytes};
+    default:
+      return {(void*)phase_update_copy<16, 16, COPY_D, 2, false>, CopyTile<16, COPY_D>::bytes};
+  }
+}
+
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 // Batched phi update over cases that qualify for copy staging: virtual
 // block b is tile (bx, by, bz) of its case, staged as in phase_update_copy.
-template <int TY, int ZC, int MINB>
+template <int TY, int ZC, int MINB, bool AL = true>
 __global__ void __launch_bounds__(TX * TY / 2, MINB)
 phase_update_batch_copy(const CaseDesc* __restrict__ cases, WorkList wl, int pc) {
   extern __shared__ __align__(16) float dsm[];
@@ -1344,7 +1439,7 @@ phase_update_batch_copy(const CaseDesc* __restrict__ cases, WorkList wl, int pc)
     const int local = b - cur.cstart;
     const int nbx = (cd.g.nx + TX - 1) / TX, nby = (cd.g.ny + TY - 1) / TY;
     __syncthreads();  // the previous tile's shared-memory reads are done
-    phase_tile_copy<TY, ZC, COPY_D>(local % nbx, (local / nbx) % nby,
+    phase_tile_copy<TY, ZC, COPY_D, AL>(local % nbx, (local / nbx) % nby,
                                     local / (nbx * nby), local, cd.phi[pc], cd.a,
                                     cd.phi[1 - pc], cd.u, cd.flags, cd.partials,
                                     cd.phase_nb, cd.g, cd.k, dsm, 0, cd.g.nz);
@@ -1395,19 +1490,32 @@ CopyKernel quad_batch_kernel(int variant) {
   }
 }
 
-CopyKernel copy_batch_kernel(int variant) {
+CopyKernel copy_batch_kernel(int variant, bool al = true) {
   switch (variant) {
-    case 1: return {(void*)phase_update_batch_copy<8, 16, 4>, CopyTile<8, COPY_D>::bytes};
-    case 2: return {(void*)phase_update_batch_copy<8, 32, 4>, CopyTile<8, COPY_D>::bytes};
-    case 3: return {(void*)phase_update_batch_copy<16, 32, 2>, CopyTile<16, COPY_D>::bytes};
-    default: return {(void*)phase_update_batch_copy<16, 16, 2>, CopyTile<16, COPY_D>::bytes};
+    case 1:
+      return {al ? (void*)phase_update_batch_copy<8, 16, 4>
+                 : (void*)phase_update_batch_copy<8, 16, 4, false>,
+              CopyTile<8, COPY_D>::bytes};
+    case 2:
+      return {al ? (void*)phase_update_batch_copy<8, 32, 4>
+                 : (void*)phase_update_batch_copy<8, 32, 4, false>,
+              CopyTile<8, COPY_D>::bytes};
+    case 3:
+      return {al ? (void*)phase_update_batch_copy<16, 32, 2>
+                 : (void*)phase_update_batch_copy<16, 32, 2, false>,
+              CopyTile<16, COPY_D>::bytes};
+    default:
+      return {al ? (void*)phase_update_batch_copy<16, 16, 2>
+                 : (void*)phase_update_batch_copy<16, 16, 2, false>,
+              CopyTile<16, COPY_D>::bytes};
   }
 }
 }  // namespace
 
 cudaError_t phase_init_attributes() {
   for (int v = 0; v < 4; ++v) {
-    for (const CopyKernel ck : {copy_kernel(v), copy_batch_kernel(v), quad_kernel(v),
+    for (const CopyKernel ck : {copy_kernel(v), copy_kernel_u(v), copy_batch_kernel(v),
+                                copy_batch_kernel(v, false), quad_kernel(v),
                                 quad_batch_kernel(v)}) {
       const cudaError_t e = cudaFuncSetAttribute(
           ck.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ck.smem);
@@ -1417,18 +1525,18 @@ cudaError_t phase_init_attributes() {
   return cudaSuccess;
 }
 
-int phase_batch_copy_occupancy(int variant) {
+int phase_batch_copy_occupancy(int variant, bool aligned) {
   int nb = 0;
   const PhaseShape s = phase_shape(variant);
-  const CopyKernel ck = copy_batch_kernel(variant);
+  const CopyKernel ck = copy_batch_kernel(variant, aligned);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ck.fn, TX * s.ty / 2, ck.smem);
   return nb;
 }
 
 cudaError_t launch_phase_batch_copy(const CaseDesc* cases, WorkList wl, int variant,
-                                    int grid, int pc, cudaStream_t st) {
+                                    int grid, int pc, bool aligned, cudaStream_t st) {
   const PhaseShape s = phase_shape(variant);
-  const CopyKernel ck = copy_batch_kernel(variant);
+  const CopyKernel ck = copy_batch_kernel(variant, aligned);
   void* args[] = {(void*)&cases, (void*)&wl, (void*)&pc};
   return cudaLaunchKernel(ck.fn, dim3(grid), dim3(TX, s.ty / 2, 1), args, ck.smem,
                           st);
@@ -1508,11 +1616,14 @@ cudaError_t launch_phase(cacl_ctx* c, const float* phi_in, float* phi_out) {
   const PhaseShape s = phase_shape(v);
   const dim3 block(TX, s.ty / 2, 1);
   const bool copy_ok = phase_copy_ok(c->g, phi_in, phi_out, c->a, c->u, c->flags);
+  // element-wise staging: any nx (nz >= 2), two nodes per thread along y
+  const bool copy_u = !copy_ok && c->g.nz >= 2;
   unsigned* ticket = c->ext_finalize ? nullptr : c->ticket;
-  if (c->phase_pipe >= 2 && !copy_ok) return cudaErrorInvalidValue;
-  if (c->phase_pipe != 1 && copy_ok) {
-    const bool two = c->phase_pipe == 2;  // two nodes per thread along y
-    const CopyKernel ck = two ? copy_kernel(v) : quad_kernel(v);
+  if (c->phase_pipe == 3 && !copy_ok) return cudaErrorInvalidValue;
+  if (c->phase_pipe == 2 && !copy_ok && !copy_u) return cudaErrorInvalidValue;
+  if (c->phase_pipe != 1 && (copy_ok || copy_u)) {
+    const bool two = c->phase_pipe == 2 || !copy_ok;  // two nodes per thread along y
+    const CopyKernel ck = !copy_ok ? copy_kernel_u(v) : (two ? copy_kernel(v) : quad_kernel(v));
     const dim3 cblock = two ? block : dim3(QTX, s.ty / 2, 1);
     const float* a = c->a;
     const float* u = c->u;

@@ -351,12 +351,15 @@ def test_phase_tile_variants(variant):
 
 
 @pytest.mark.parametrize("variant", [0, 1, 2, 3])
-@pytest.mark.parametrize("shape", [(68, 37, 45), (12, 20, 9)])
+@pytest.mark.parametrize("shape", [(68, 37, 45), (12, 20, 9), (37, 21, 19), (70, 9, 34),
+                                   (5, 12, 6)])
 def test_phase_copy_pipeline(variant, shape):
-    """The phase update staged by asynchronous 16-byte copies (nx a multiple
-    of 4) gives bit for bit the phi* and partial sums of the register-staged
-    update, and the oracle's phi*, on ragged tiles and on a grid narrower
-    than the staged window (x wraps several times inside it)."""
+    """The phase update staged by asynchronous copies (16-byte copies when nx
+    is a multiple of 4; 4-byte copies element by element with the flag bytes
+    staged through registers when nx is odd or 2 mod 4) gives bit for bit
+    the phi* and partial sums of the register-staged update, and the
+    oracle's phi*, on ragged tiles and on grids narrower than the staged
+    window (x wraps several times inside it)."""
     from paper_2607_25444_b300 import cacl
     nx, ny, nz = shape
     p, solid, phi = _droplet_case(nx=nx, ny=ny, nz=nz, theta=50.0)
@@ -437,13 +440,21 @@ def test_phase_quad_pipeline(variant, shape):
 
 
 def test_phase_copy_pipeline_rejects_unaligned_nx():
+    """The 2 x 2 update needs nx % 4 == 0; the two-node copy-staged update
+    takes any nx but needs nz >= 2 (planes are wrapped once)."""
     from paper_2607_25444_b300 import cacl
     p, solid, phi = _droplet_case(nx=70, ny=37, nz=45, theta=50.0)
     g = _solver(p)
+    with pytest.raises(cacl.CaclError):
+        g.set_option(cacl.OPT_PHASE_PIPE, 3)
+    g.set_option(cacl.OPT_PHASE_PIPE, 2)
+    g.set_option(cacl.OPT_PHASE_PIPE, 0)
+    q = I.base_params(12, 10, 1, periodic=(1, 1, 1))
+    h = _solver(q)
     for pipe in (2, 3):
         with pytest.raises(cacl.CaclError):
-            g.set_option(cacl.OPT_PHASE_PIPE, pipe)
-    g.set_option(cacl.OPT_PHASE_PIPE, 0)
+            h.set_option(cacl.OPT_PHASE_PIPE, pipe)
+    h.set_option(cacl.OPT_PHASE_PIPE, 1)
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
