@@ -88,3 +88,46 @@ def test_all_solid_grid():
     assert m["m_ref"] == 0.0 and m["lam"] == 0.0
     assert np.array_equal(g.fields()[0], phi)
     g.close()
+
+
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(ny=-3), dict(width=0.0), dict(rho_g=0.0),
+                                 dict(nu_l=-0.1), dict(eps_phi=0.5), dict(sigma=-1.0),
+                                 dict(storage=7)])
+def test_invalid_parameters_are_rejected(bad):
+    """An empty or negative grid, a non-positive width, density or viscosity,
+    a band threshold outside (0, 1/2), a negative surface tension and an
+    unknown storage are refused at creation, before any device memory is
+    taken."""
+    from paper_2607_25444_b300 import cacl
+    p = I.base_params(8, 8, 8)
+    p.update(bad)
+    with pytest.raises(cacl.CaclError):
+        cacl.Solver(p)
+
+
+def test_zero_steps_and_single_node_rows():
+    """step(0) changes nothing; a grid one node wide in x and y (every
+    neighbour wraps onto the node itself) steps like the oracle."""
+    nx, ny, nz = 1, 1, 12
+    p = I.base_params(nx, ny, nz, sigma=0.01, rho_l=1.0, rho_g=0.2, nu_l=0.05,
+                      nu_g=0.1, theta_deg=70.0, gravity=(0.0, 0.0, -1e-5))
+    solid = I.walls_z(nx, ny, nz)
+    phi = np.zeros((nz, ny, nx), np.float32)
+    phi[1:6] = 1.0
+    phi[6] = 0.5
+    from paper_2607_25444_b300 import cacl
+    g = cacl.Solver(p)
+    g.set_geometry(solid)
+    g.set_fields(phi)
+    before = [x.copy() for x in g.fields()]
+    g.step(0)
+    for a, b in zip(before, g.fields()):
+        assert np.array_equal(a, b)
+    g.close()
+    g, o = _pair(p, solid, phi, 10)
+    fluid = solid == 0
+    gp, gu, _ = g.fields()
+    op, ou, _ = o.fields()
+    assert np.abs(gp[fluid] - op[fluid]).max() < 1e-5
+    assert np.abs(gu[:, fluid] - ou[:, fluid]).max() < 1e-5 * max(np.abs(ou).max(), 1e-12) + 1e-9
+    g.close()
