@@ -89,3 +89,17 @@ def test_unaligned_slabs_agree_to_rounding():
     ref, got = _run(p, solid, phi, None, 3, 20, aligned=False)
     assert np.abs(ref[0] - got[0]).max() < 1e-5
     assert np.abs(ref[1] - got[1]).max() < 1e-6
+
+
+def test_slabs_bit_identical_odd_nx():
+    """nx = 23 (the phi update staged element by element, one node per
+    thread in the collide-stream) and ny = 18: 2 slabs of 32 planes, walls,
+    a drop on the bottom wall reaching the cut, 25 steps, bit-identical."""
+    nx, ny, nz = 23, 18, 64
+    p = I.base_params(nx, ny, nz, sigma=0.01, rho_g=0.25, nu_g=0.1,
+                      theta_deg=75.0, gravity=(0.0, 0.0, -1e-5))
+    solid = I.walls_z(nx, ny, nz)
+    phi = I.droplet(nx, ny, nz, (11.5, 9.0, 0.5), 30.0, p["width"])
+    ref, got = _run(p, solid, phi, None, 2, 25)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
