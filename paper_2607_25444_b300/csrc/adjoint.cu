@@ -503,19 +503,11 @@ __device__ __forceinline__ void collide_adj(const float (&f)[Q], float phi0,
   o.phi0b = phi0b;
 }
 
-// FP64 sum of one value per thread of a 128-thread block (warp shuffles,
-// then the four warp sums in order); the result is valid in thread 0.
-__device__ __forceinline__ double block128_sum(double v, double* sh4) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-  if ((threadIdx.x & 31) == 0) sh4[threadIdx.x >> 5] = v;
-  __syncthreads();
-  return (sh4[0] + sh4[1]) + (sh4[2] + sh4[3]);
-}
-
 // Per fluid node: the collision recomputed from the taped pull and reversed.
-// Block = 128 nodes of one x row (blockIdx.y = y, blockIdx.z = z); the
-// block's dL/dsigma share is added to sig_acc[block].
+// Block = 128 nodes of one x row (blockIdx.y = y, blockIdx.z = z); each
+// warp's dL/dsigma share is added to its own slot sig_acc[4 block + warp]
+// (no block barrier: a warp that finishes early, or holds only nodes past
+// the row's end, leaves at once).
 // The adjoint of the node's post-collision populations f*_q(n) is gathered
 // from the pulled-population adjoints of the later step (finb_later, or
 // zero when null) through the transpose of the pull: f*_q(n) fed
@@ -529,7 +521,6 @@ adj_lb_node(const float* __restrict__ fprev, const float* __restrict__ phig,
             float* __restrict__ finb, float* __restrict__ nodeb,
             double* __restrict__ sig_acc, Grid g, Consts k, float dbeta4_dsigma,
             float dkphi_dsigma) {
-  __shared__ double sh4[4];
   const int x = blockIdx.x * 128 + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;
   const IDX N = (IDX)g.N;
@@ -582,11 +573,13 @@ adj_lb_node(const float* __restrict__ fprev, const float* __restrict__ phig,
 #pragma unroll
     for (int c = 0; c < 5; ++c) nodeb[c * N + n] = 0.f;
   }
-  const double tot = block128_sum(sig, sh4);
-  // each block owns one accumulator slot: the steps add to it in turn and
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sig += __shfl_down_sync(0xffffffffu, sig, off);
+  // each warp owns one accumulator slot: the steps add to it in turn and
   // the slots are summed once after the last step
-  if (threadIdx.x == 0)
-    sig_acc[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] += tot;
+  if ((threadIdx.x & 31) == 0)
+    sig_acc[4 * (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)) +
+            (threadIdx.x >> 5)] += sig;
 }
 
 // Transpose of the phi stencil (gradient, Laplacian, own value) of the
@@ -975,7 +968,7 @@ cacl_status cacl_adjoint_forward_levels(cacl_ctx* c, int nsteps, int every,
     ACK(alloc(&s->sigmab, 1), "alloc adjoint");
     s->npart = std::max((int)(((c->g.nx + 127) / 128) * (int64_t)c->g.ny * c->g.nz), 1024);
     ACK(alloc(&s->partial, s->npart), "alloc adjoint");
-    ACK(alloc(&s->sig_acc, s->npart), "alloc adjoint");
+    ACK(alloc(&s->sig_acc, 4 * (size_t)s->npart), "alloc adjoint");  // per warp
     ACK(alloc(&s->scal, 2), "alloc adjoint");
     const cacl_status st = build_transpose(c, s);
     if (st != CACL_OK) return st;
@@ -1039,7 +1032,7 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
       "seed");
   ACK(cudaMemsetAsync(s->thetab, 0, sizeof(double) * (W > 0 ? W : 1), st), "seed");
   ACK(cudaMemsetAsync(s->sigmab, 0, sizeof(double), st), "seed");
-  const int nbl_all = (int)(((g.nx + 127) / 128) * (int64_t)g.ny * g.nz);
+  const int nbl_all = 4 * (int)(((g.nx + 127) / 128) * (int64_t)g.ny * g.nz);  // warps
   ACK(cudaMemsetAsync(s->sig_acc, 0, sizeof(double) * nbl_all, st), "seed");
 
   const bool small = !c->index64 && (int64_t)Q * N < (int64_t)INT32_MAX;  // 32-bit offsets
@@ -1060,35 +1053,37 @@ cacl_status cacl_adjoint_backward(cacl_ctx* c, const float* dL_dphi,
                                                   eps, s->scal, s->phisb);
     // A2 phi update
     const dim3 rows((g.nx + 127) / 128, g.ny, g.nz);
+    // threads of a row block: 128, or the row rounded up to whole warps
+    const int rt = std::min(128, (g.nx + 31) / 32 * 32);
     if (small15) {
-      adj_phase_faces<int><<<rows, 128, 0, st>>>(s->t_phig[t], s->t_u[t], c->flags,
+      adj_phase_faces<int><<<rows, rt, 0, st>>>(s->t_phig[t], s->t_u[t], c->flags,
                                                  s->phisb, s->face, g);
-      adj_phase_gather<int><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face, s->phigb,
+      adj_phase_gather<int><<<rows, rt, 0, st>>>(c->flags, s->phisb, s->face, s->phigb,
                                                   s->ub, s->ab, g, c->k);
     } else {
-      adj_phase_faces<int64_t><<<rows, 128, 0, st>>>(s->t_phig[t], s->t_u[t], c->flags,
+      adj_phase_faces<int64_t><<<rows, rt, 0, st>>>(s->t_phig[t], s->t_u[t], c->flags,
                                                      s->phisb, s->face, g);
-      adj_phase_gather<int64_t><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face,
+      adj_phase_gather<int64_t><<<rows, rt, 0, st>>>(c->flags, s->phisb, s->face,
                                                       s->phigb, s->ub, s->ab, g, c->k);
     }
     // A3 collide-stream; the later step's pulled-population adjoints (none
     // after the last step)
     const float* later = first ? nullptr : s->fb;
     if (small) {
-      adj_lb_node<int><<<rows, 128, 0, st>>>(s->t_fprev[t], s->t_phig[t], c->flags, later,
+      adj_lb_node<int><<<rows, rt, 0, st>>>(s->t_fprev[t], s->t_phig[t], c->flags, later,
                                              s->ub, s->ab, s->fb2, s->nodeb, s->sig_acc, g,
                                              c->k, db4, dkp);
     } else {
-      adj_lb_node<int64_t><<<rows, 128, 0, st>>>(s->t_fprev[t], s->t_phig[t], c->flags,
+      adj_lb_node<int64_t><<<rows, rt, 0, st>>>(s->t_fprev[t], s->t_phig[t], c->flags,
                                                  later, s->ub, s->ab, s->fb2, s->nodeb,
                                                  s->sig_acc, g, c->k, db4, dkp);
     }
     std::swap(s->fb, s->fb2);  // fb: this step's pulled-population adjoints
     first = false;
     if (small)
-      adj_lb_gather<int><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
+      adj_lb_gather<int><<<rows, rt, 0, st>>>(s->nodeb, s->phigb, g);
     else
-      adj_lb_gather<int64_t><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
+      adj_lb_gather<int64_t><<<rows, rt, 0, st>>>(s->nodeb, s->phigb, g);
     // A4 ghost map
     if (W > 0)
       adj_ghost_node<<<nblk(W, 128), 128, 0, st>>>(s->t_phipre[t], c->w_idx, c->w_donor,
@@ -1285,6 +1280,8 @@ cacl_status cacl_adjoint_stage(cacl_ctx* c, int stage, const float* in, float* o
     }
   }
   const dim3 rows((g.nx + 127) / 128, g.ny, g.nz);
+  // threads of a row block: 128, or the row rounded up to whole warps
+  const int rt = std::min(128, (g.nx + 31) / 32 * 32);
   const bool small = !c->index64 && (int64_t)Q * N < (int64_t)INT32_MAX;
   const bool small15 = !c->index64 && (int64_t)15 * N < (int64_t)INT32_MAX;
   switch (stage) {
@@ -1302,14 +1299,14 @@ cacl_status cacl_adjoint_stage(cacl_ctx* c, int stage, const float* in, float* o
     case CACL_ADJ_PHASE:
       ACK(cudaMemcpyAsync(s->phisb, in, pb, cudaMemcpyDeviceToDevice, st), "in");
       if (small15) {
-        adj_phase_faces<int><<<rows, 128, 0, st>>>(s->t_phig[0], s->t_u[0], c->flags,
+        adj_phase_faces<int><<<rows, rt, 0, st>>>(s->t_phig[0], s->t_u[0], c->flags,
                                                    s->phisb, s->face, g);
-        adj_phase_gather<int><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face, s->phigb,
+        adj_phase_gather<int><<<rows, rt, 0, st>>>(c->flags, s->phisb, s->face, s->phigb,
                                                     s->ub, s->ab, g, c->k);
       } else {
-        adj_phase_faces<int64_t><<<rows, 128, 0, st>>>(s->t_phig[0], s->t_u[0], c->flags,
+        adj_phase_faces<int64_t><<<rows, rt, 0, st>>>(s->t_phig[0], s->t_u[0], c->flags,
                                                        s->phisb, s->face, g);
-        adj_phase_gather<int64_t><<<rows, 128, 0, st>>>(c->flags, s->phisb, s->face,
+        adj_phase_gather<int64_t><<<rows, rt, 0, st>>>(c->flags, s->phisb, s->face,
                                                         s->phigb, s->ub, s->ab, g, c->k);
       }
       ACK(cudaMemcpyAsync(out, s->phigb, pb, cudaMemcpyDeviceToDevice, st), "out");
@@ -1321,19 +1318,19 @@ cacl_status cacl_adjoint_stage(cacl_ctx* c, int stage, const float* in, float* o
       ACK(cudaMemcpyAsync(s->ub, in + Q * N, 3 * pb, cudaMemcpyDeviceToDevice, st), "in");
       ACK(cudaMemcpyAsync(s->ab, in + (Q + 3) * N, 3 * pb, cudaMemcpyDeviceToDevice, st),
           "in");
-      const int nbl_all = (int)(((g.nx + 127) / 128) * (int64_t)g.ny * g.nz);
+      const int nbl_all = 4 * (int)(((g.nx + 127) / 128) * (int64_t)g.ny * g.nz);
       ACK(cudaMemsetAsync(s->sig_acc, 0, sizeof(double) * nbl_all, st), "zero");
       ACK(cudaMemsetAsync(s->phigb, 0, pb, st), "zero");
       if (small) {
-        adj_lb_node<int><<<rows, 128, 0, st>>>(s->t_fprev[0], s->t_phig[0], c->flags, s->fb,
+        adj_lb_node<int><<<rows, rt, 0, st>>>(s->t_fprev[0], s->t_phig[0], c->flags, s->fb,
                                                s->ub, s->ab, s->fb2, s->nodeb, s->sig_acc,
                                                g, c->k, db4, dkp);
-        adj_lb_gather<int><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
+        adj_lb_gather<int><<<rows, rt, 0, st>>>(s->nodeb, s->phigb, g);
       } else {
-        adj_lb_node<int64_t><<<rows, 128, 0, st>>>(s->t_fprev[0], s->t_phig[0], c->flags,
+        adj_lb_node<int64_t><<<rows, rt, 0, st>>>(s->t_fprev[0], s->t_phig[0], c->flags,
                                                    s->fb, s->ub, s->ab, s->fb2, s->nodeb,
                                                    s->sig_acc, g, c->k, db4, dkp);
-        adj_lb_gather<int64_t><<<rows, 128, 0, st>>>(s->nodeb, s->phigb, g);
+        adj_lb_gather<int64_t><<<rows, rt, 0, st>>>(s->nodeb, s->phigb, g);
       }
       sum_partials<<<1, 128, 0, st>>>(s->sig_acc, nbl_all, s->sigmab);
       ACK(cudaMemcpyAsync(out, s->fb2, pb * Q, cudaMemcpyDeviceToDevice, st), "out");
