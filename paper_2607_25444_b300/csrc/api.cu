@@ -273,8 +273,8 @@ cacl_status cacl_set_fields(cacl_ctx* c, const float* phi, const float* u) {
   const int64_t N = c->g.N;
   CK(cudaMemcpyAsync(c->phi[0], phi, sizeof(float) * N, cudaMemcpyHostToDevice,
                      c->stream), "upload phi");
-  CK(cudaMemcpyAsync(c->phi[1], phi, sizeof(float) * N, cudaMemcpyHostToDevice,
-                     c->stream), "upload phi");
+  CK(cudaMemcpyAsync(c->phi[1], c->phi[0], sizeof(float) * N, cudaMemcpyDeviceToDevice,
+                     c->stream), "copy phi");
   if (u)
     CK(cudaMemcpyAsync(c->u, u, sizeof(float) * 3 * N, cudaMemcpyHostToDevice,
                        c->stream), "upload u");
