@@ -366,7 +366,8 @@ cacl_status cacl_batch_autotune(cacl_batch* batch, int steps, int* lb_variant,
  * kernel, as when 27 N >= 2^31), whatever the grid size; the results are
  * bit-identical to pipeline 2 (or 1) and to the 32-bit adjoint. It exists so
  * that the path of grids above 2^31 / 27 nodes can be checked on small
- * ones. Defaults: tile 2, pipelines 0, index64 0.
+ * ones. Defaults: tile 2 (tile 1 when the grid has fewer than 400 tiles
+ * of 32 x 8 x 32 nodes), pipelines 0, index64 0.
  * Returns CACL_ERR_ARG for an unknown option or value. */
 typedef enum {
   CACL_OPT_PHASE_TILE = 1,

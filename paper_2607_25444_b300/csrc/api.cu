@@ -164,6 +164,7 @@ cacl_status cacl_create(const cacl_params* p, void* stream, cacl_ctx** out) {
     return bail("alloc a");
   if ((e = cudaMalloc(&c->flags, N)) != cudaSuccess) return bail("alloc flags");
   if ((e = lb_tma_init(c)) != cudaSuccess) return bail("collide-stream tensor maps");
+  c->phase_variant = phase_default_variant(c->g);
   c->part_blocks = phase_blocks(c);
   const int pb = std::max(c->part_blocks, mass_ref_blocks(N));
   if ((e = cudaMalloc(&c->partials, sizeof(double) * 2 * pb)) != cudaSuccess)

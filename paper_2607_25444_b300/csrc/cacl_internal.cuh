@@ -505,6 +505,7 @@ cudaError_t launch_to_storage(cacl_ctx* c, const float* src, void* dst);
 cudaError_t launch_from_storage(cacl_ctx* c, const void* src, float* dst);
 cudaError_t launch_check_finite(cacl_ctx* c, const float* phi, int* bad_dev);
 int phase_blocks(const cacl_ctx* c);
+int phase_default_variant(const Grid& g);
 int mass_ref_blocks(int64_t N);
 void adjoint_free(AdjointState* s);
 

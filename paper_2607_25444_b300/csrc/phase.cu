@@ -1379,6 +1379,16 @@ dim3 phase_grid(const Grid& g, int variant, int nzr) {
 
 }  // namespace
 
+// The default tile shape: 32 x 8 x 32 (variant 2), or 32 x 8 x 16 (variant
+// 1) when the deeper tiles would number fewer than 400, fewer than three
+// per SM, and leave most of the GPU idle (measured per step: 64^3 45.4 ->
+// 36.9 us, 96^3 87.0 -> 80.5, 128^3 130.6 -> 127.9; from 160^3 on the deeper
+// tiles are faster).
+int phase_default_variant(const Grid& g) {
+  const dim3 gr = phase_grid(g, 2, g.nz);
+  return (int64_t)gr.x * gr.y * gr.z < 400 ? 1 : 2;
+}
+
 int phase_blocks(const cacl_ctx* c) {
   // partial-sum storage is sized for the variant with the most blocks
   int nb = 0;

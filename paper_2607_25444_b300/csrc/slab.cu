@@ -81,6 +81,11 @@ cacl_status cacl_slab_create(const cacl_params* global, int z0, int nz,
   c->node_offset = nxy * (int64_t)(z0 - HALO);
   c->slab_z0 = z0;
   c->slab_nz = nz;
+  // the tile shape the undivided grid takes by default, so that the slabs'
+  // tiles and partial sums match its own
+  c->phase_variant = phase_default_variant(
+      {global->nx, global->ny, global->nz,
+       (int64_t)global->nx * global->ny * global->nz});
   *out = c;
   return CACL_OK;
 }
