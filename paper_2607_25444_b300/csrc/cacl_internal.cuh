@@ -78,9 +78,25 @@ struct StoreF16 {
   __device__ __forceinline__ static T2 encode_w2(float2 P, int q) {
     return __float22half2_rn(P);
   }
-  __device__ __forceinline__ static T2 pack(T lo, T hi) { return __halves2half2(lo, hi); }
-  __device__ __forceinline__ static T lo(T2 v) { return __low2half(v); }
-  __device__ __forceinline__ static T hi(T2 v) { return __high2half(v); }
+  // pair assembly on the bits (a byte permutation, a mask or a shift)
+  __device__ __forceinline__ static uint32_t bits2(T2 v) {
+    return *reinterpret_cast<const uint32_t*>(&v);
+  }
+  __device__ __forceinline__ static uint32_t bits1(T v) {
+    return *reinterpret_cast<const uint16_t*>(&v);
+  }
+  __device__ __forceinline__ static T2 pack(T lo, T hi) {
+    const uint32_t b = __byte_perm(bits1(lo), bits1(hi), 0x5410);
+    return *reinterpret_cast<const T2*>(&b);
+  }
+  __device__ __forceinline__ static T lo(T2 v) {
+    const uint16_t b = (uint16_t)(bits2(v) & 0xffffu);
+    return *reinterpret_cast<const T*>(&b);
+  }
+  __device__ __forceinline__ static T hi(T2 v) {
+    const uint16_t b = (uint16_t)(bits2(v) >> 16);
+    return *reinterpret_cast<const T*>(&b);
+  }
 };
 
 struct StoreBF16 {
@@ -95,18 +111,35 @@ struct StoreBF16 {
   __device__ __forceinline__ static T encode_w(float P, int q) {
     return __float2bfloat16_rn(P);
   }
+  // a bf16 value is the upper half of the float it widens to: the pair
+  // operations below work on the bits (exact, the same values as the
+  // conversion intrinsics)
+  __device__ __forceinline__ static uint32_t bits2(T2 v) {
+    return *reinterpret_cast<const uint32_t*>(&v);
+  }
+  __device__ __forceinline__ static uint32_t bits1(T v) {
+    return *reinterpret_cast<const uint16_t*>(&v);
+  }
   __device__ __forceinline__ static float2 decode2(T2 v, int q) {
-    const float2 h = __bfloat1622float2(v);
-    return make_float2(__fmul_rn(h.x, wq(q)), __fmul_rn(h.y, wq(q)));
+    const uint32_t b = bits2(v);
+    return make_float2(__fmul_rn(__uint_as_float(b << 16), wq(q)),
+                       __fmul_rn(__uint_as_float(b & 0xffff0000u), wq(q)));
   }
   __device__ __forceinline__ static T2 encode_w2(float2 P, int q) {
     return __float22bfloat162_rn(P);
   }
   __device__ __forceinline__ static T2 pack(T lo, T hi) {
-    return __halves2bfloat162(lo, hi);
+    const uint32_t b = __byte_perm(bits1(lo), bits1(hi), 0x5410);
+    return *reinterpret_cast<const T2*>(&b);
   }
-  __device__ __forceinline__ static T lo(T2 v) { return __low2bfloat16(v); }
-  __device__ __forceinline__ static T hi(T2 v) { return __high2bfloat16(v); }
+  __device__ __forceinline__ static T lo(T2 v) {
+    const uint16_t b = (uint16_t)(bits2(v) & 0xffffu);
+    return *reinterpret_cast<const T*>(&b);
+  }
+  __device__ __forceinline__ static T hi(T2 v) {
+    const uint16_t b = (uint16_t)(bits2(v) >> 16);
+    return *reinterpret_cast<const T*>(&b);
+  }
 };
 
 inline size_t storage_bytes(int storage) {
