@@ -805,9 +805,9 @@ lb_collide(const typename Store::T* __restrict__ fin,
 // Four x-adjacent nodes per thread for 16-bit populations (nx a multiple
 // of 4): one 8-byte load per population of the quad (its pairs A = (x0,
 // x0+1) and B = (x0+2, x0+3)), the element left of and right of the quad
-// from 2-byte loads (x wraps), one 16-byte load per phi row, and 4-byte
-// stores of each pair's populations. Each pair is
-// evaluated exactly as in lb_pair, so the result is bit-identical; the
+// from 2-byte loads (x wraps), one 16-byte load per phi row, and one
+// 8-byte store per population of the quad (both pairs together). Each pair
+// is evaluated exactly as in lb_pair, so the result is bit-identical; the
 // address arithmetic of a population, phi row or field serves four nodes.
 template <typename Store>
 __device__ __forceinline__ void lb_quad(int x0, int y, int z,
@@ -914,10 +914,11 @@ __device__ __forceinline__ void lb_quad(int x0, int y, int z,
 // Block (LBQ_PX, LBQ_PY): 4 LBQ_PX nodes of LBQ_PY rows. A quad with a solid
 // node or a wall neighbour runs the one-node path on each node. Bounded to
 // 128 registers (eight blocks of 64 threads per SM; ptxas spills about 70
-// bytes). FP16 at 256^3: 0.474 ms per launch; 0.479 with four blocks of 128
-// threads, 0.474 at 168 registers (BF16 0.513 there, 0.480 here), 0.511
-// when each pair's populations were stored as soon as the pair was done
-// (4-byte stores) rather than together (8-byte stores).
+// bytes). FP16 at 256^3: 0.464 ms per launch (BF16 0.459); before the
+// shifted pairs were assembled on the bits, 0.474 here against 0.479 with
+// four blocks of 128 threads and 0.474 at 168 registers (BF16 0.513 there,
+// 0.480 here), and 0.511 when each pair's populations were stored as soon
+// as the pair was done (4-byte stores) rather than together (8-byte stores).
 constexpr int LBQ_PX = 32;
 constexpr int LBQ_PY = 2;
 template <typename Store>
