@@ -181,6 +181,18 @@ cacl_status cacl_load_state(cacl_ctx* ctx, const void* host_buf, int64_t bytes);
  * word stays set: the state is not trusted after such a failure. */
 cacl_status cacl_inject_wait_timeout(cacl_ctx* ctx);
 
+/* Test hook that makes a bounded wait run out (no GPU fault is made). While
+ * on != 0, every block of the copy-staged collide-stream
+ * (CACL_OPT_LB_PIPE = 1) registers 16 bytes more for the copies of its
+ * first row segment than they deliver, so the wait for them cannot
+ * complete: each thread gives up after 0.5 s of the GPU's global timer,
+ * the block records it in the device error word, finishes its segment on
+ * the stale stage, waits (bounded) for its copies still in flight and
+ * returns. The next cacl_check_finite returns CACL_ERR_TIMEOUT; the word
+ * stays set and the state is not trusted. Other kernels ignore the
+ * request. Synchronises the context stream. */
+cacl_status cacl_inject_copy_stall(cacl_ctx* ctx, int on);
+
 /* Advance nsteps >= 0 full steps (ghost update, collide-stream, phi update,
  * volume correction) on the context stream; does not synchronise. The
  * step's correction visits only the phi-update tiles whose chi sum is

@@ -33,7 +33,7 @@ EXPORTS = (
     "cacl_batch_autotune", "cacl_set_wall_angles", "cacl_set_sigma",
     "cacl_adjoint_forward", "cacl_adjoint_forward_levels", "cacl_adjoint_backward",
     "cacl_adjoint_timing", "cacl_adjoint_stage", "cacl_state_bytes", "cacl_save_state",
-    "cacl_load_state", "cacl_inject_wait_timeout", "cacl_slab_create", "cacl_slab_stage", "cacl_slab_partials", "cacl_slab_correct",
+    "cacl_load_state", "cacl_inject_wait_timeout", "cacl_inject_copy_stall", "cacl_slab_create", "cacl_slab_stage", "cacl_slab_partials", "cacl_slab_correct",
     "cacl_slab_halo", "cacl_slab_halo_bytes",
 )
 OPT_PHASE_TILE = 1
@@ -125,6 +125,7 @@ def load():
     L.cacl_save_state.argtypes = [vp, vp, C.c_int64]
     L.cacl_load_state.argtypes = [vp, vp, C.c_int64]
     L.cacl_inject_wait_timeout.argtypes = [vp]
+    L.cacl_inject_copy_stall.argtypes = [vp, C.c_int]
     L.cacl_slab_create.argtypes = [C.POINTER(CaclParams), C.c_int, C.c_int, vp,
                                    C.POINTER(vp)]
     L.cacl_slab_stage.argtypes = [vp, C.c_int]
@@ -412,6 +413,11 @@ class Solver:
     def inject_wait_timeout(self):
         """Test hook: mark the context as if a copy wait had given up."""
         self._check(self.L.cacl_inject_wait_timeout(self.h))
+
+    def inject_copy_stall(self, on=True):
+        """Test hook: make the copy-staged collide-stream's first waits run
+        out (CACL_OPT_LB_PIPE = 1; each after 0.5 s)."""
+        self._check(self.L.cacl_inject_copy_stall(self.h, 1 if on else 0))
 
     def adjoint_timing(self):
         """GPU milliseconds of the last backward: (recompute, total)."""

@@ -173,9 +173,9 @@ cacl_status cacl_create(const cacl_params* p, void* stream, cacl_ctx** out) {
     return bail("alloc mass");
   if ((e = cudaMalloc(&c->bad_flag, sizeof(int))) != cudaSuccess)
     return bail("alloc flag");
-  if ((e = cudaMalloc(&c->ticket, 2 * sizeof(unsigned))) != cudaSuccess)
+  if ((e = cudaMalloc(&c->ticket, 3 * sizeof(unsigned))) != cudaSuccess)
     return bail("alloc ticket");
-  if ((e = cudaMemsetAsync(c->ticket, 0, 2 * sizeof(unsigned), c->stream)) !=
+  if ((e = cudaMemsetAsync(c->ticket, 0, 3 * sizeof(unsigned), c->stream)) !=
       cudaSuccess)
     return bail("memset");
   if ((e = cudaMemsetAsync(c->mass, 0, sizeof(MassScalars), c->stream)) !=
@@ -466,6 +466,16 @@ cacl_status cacl_inject_wait_timeout(cacl_ctx* c) {
   if (!c->ticket) return fail(c, CACL_ERR_STATE, "context without device state");
   const unsigned one = 1u;
   CK(cudaMemcpyAsync(c->ticket + 1, &one, sizeof one, cudaMemcpyHostToDevice, c->stream),
+     "inject");
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  return CACL_OK;
+}
+
+cacl_status cacl_inject_copy_stall(cacl_ctx* c, int on) {
+  if (!c) return CACL_ERR_ARG;
+  if (!c->ticket) return fail(c, CACL_ERR_STATE, "context without device state");
+  const unsigned v = on ? 1u : 0u;
+  CK(cudaMemcpyAsync(c->ticket + 2, &v, sizeof v, cudaMemcpyHostToDevice, c->stream),
      "inject");
   CK(cudaStreamSynchronize(c->stream), "sync");
   return CACL_OK;

@@ -572,12 +572,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 // Bounded wait for phase `parity` of the barrier, sleeping between tests
-// so that a waiting warp leaves the issue slots to the others: false after
-// the limit (about 0.5 s).
+// so that a waiting warp leaves the issue slots to the others: false once
+// 0.5 s have passed on the global timer (or after 2^22 tests, whichever
+// comes first, whatever time one test takes).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int i = 0; i < (1 << 20); ++i) {
+  const uint64_t t0 = global_ns();
+  for (int i = 0; i < (1 << 22); ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > 500000000ull) return false;
     __nanosleep(200);
   }
   return false;
@@ -693,6 +702,9 @@ lb_collide_staged(const typename Store::T* __restrict__ fin,
                   const float* __restrict__ phi, float* __restrict__ u,
                   float* __restrict__ a, const uint8_t* __restrict__ flags,
                   Grid g, Consts k, int nseg, unsigned* __restrict__ wait_err) {
+  // wait_err[0]: set when a wait gave up; wait_err[1]: test request
+  // (cacl_inject_copy_stall) to register 16 bytes more for the first
+  // segment than its copies deliver, so that its wait cannot complete
   using R = StagedRows<Store>;
   extern __shared__ __align__(16) unsigned char lb_smem[];
   R* st = reinterpret_cast<R*>(lb_smem);  // [2]
@@ -709,7 +721,9 @@ lb_collide_staged(const typename Store::T* __restrict__ fin,
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     s_fail = 0;
-    if (s < nseg) mbar_arrive_expect_tx(&bar[0], staged_bytes<Store>(segment_of(s, g).L));
+    if (s < nseg)
+      mbar_arrive_expect_tx(&bar[0], staged_bytes<Store>(segment_of(s, g).L) +
+                                         (wait_err[1] ? 16u : 0u));
     if (s + G < nseg)
       mbar_arrive_expect_tx(&bar[1], staged_bytes<Store>(segment_of(s + G, g).L));
   }
@@ -733,7 +747,8 @@ lb_collide_staged(const typename Store::T* __restrict__ fin,
     if (s + G < nseg)
       staged_issue<Store, IDX>(st[cur ^ 1], &bar[cur ^ 1], nxt, tid, fin, phi, g,
                                fl_, fr_, pl, pr);
-    if (!mbar_wait(&bar[cur], (i >> 1) & 1)) {
+    const bool arrived = mbar_wait(&bar[cur], (i >> 1) & 1);
+    if (!arrived) {
       s_fail = 1;
       atomicOr(wait_err, 1u);
     }
@@ -776,8 +791,10 @@ lb_collide_staged(const typename Store::T* __restrict__ fin,
       }
     }
     // register the bytes of the segment after next, whose copies go to this
-    // stage once every thread is past the barrier below
-    if (tid == 0 && s + 2 * G < nseg)
+    // stage once every thread is past the barrier below (not after a wait
+    // that gave up: the barrier's phase is still open, and a second arrival
+    // on it is not allowed)
+    if (tid == 0 && arrived && s + 2 * G < nseg)
       mbar_arrive_expect_tx(&bar[cur], staged_bytes<Store>(segment_of(s + 2 * G, g).L));
     if (s + G < nseg) staged_pads<Store>(st[cur ^ 1], nxt.L, tid, fl_, fr_, pl, pr);
     __syncthreads();

@@ -2,7 +2,8 @@
 restored from a saved state steps on bit for bit like the one it was saved
 from, including the unbiased rounding of the volume correction (Sect. 2.3),
 whose key is part of the state; and the failure-detection path of a copy
-wait that gave up, exercised by setting its error word from the host."""
+wait that gave up, exercised by setting its error word from the host and by
+making the bounded wait itself run out on the GPU (no fault is made)."""
 import numpy as np
 import pytest
 
@@ -87,3 +88,46 @@ def test_injected_wait_timeout_is_reported():
         s.check_finite()
     assert e.value.status == -6  # CACL_ERR_TIMEOUT
     s.close()
+
+
+def test_copy_wait_runs_out_and_is_reported():
+    """The copy-staged collide-stream's bounded wait made to run out (each
+    block registers 16 bytes more than its first copies deliver): the step
+    ends after the wait's 0.5-s limit, cacl_check_finite reports
+    CACL_ERR_TIMEOUT, and the device stays usable: a new context with the
+    same pipeline steps bit for bit like the default pipeline."""
+    import time
+    from paper_2607_25444_b300 import cacl
+    p, solid, phi = _case("f32")
+    s = _solver(p, solid)
+    s.set_option(cacl.OPT_LB_PIPE, 1)
+    s.set_fields(phi)
+    s.step(2)
+    s.check_finite()
+    s.fields()
+    s.inject_copy_stall(True)
+    t0 = time.perf_counter()
+    s.step(1)
+    s.fields()  # waits for the step
+    dt = time.perf_counter() - t0
+    with pytest.raises(cacl.CaclError) as e:
+        s.check_finite()
+    assert e.value.status == -6  # CACL_ERR_TIMEOUT
+    assert 0.45 < dt < 30.0, dt
+    s.inject_copy_stall(False)
+    s.close()
+
+    a = _solver(p, solid)
+    a.set_option(cacl.OPT_LB_PIPE, 1)
+    a.set_fields(phi)
+    a.step(3)
+    a.check_finite()
+    b = _solver(p, solid)
+    b.set_fields(phi)
+    b.step(3)
+    fluid = solid == 0
+    (pa, ua, _), (pb, ub, _) = a.fields(), b.fields()
+    assert np.array_equal(pa[fluid], pb[fluid])
+    assert np.array_equal(ua[:, fluid], ub[:, fluid])
+    a.close()
+    b.close()
