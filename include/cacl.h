@@ -188,9 +188,12 @@ cacl_status cacl_inject_wait_timeout(cacl_ctx* ctx);
  * complete: each thread gives up after 0.5 s of the GPU's global timer,
  * the block records it in the device error word, finishes its segment on
  * the stale stage, waits (bounded) for its copies still in flight and
- * returns. The next cacl_check_finite returns CACL_ERR_TIMEOUT; the word
- * stays set and the state is not trusted. Other kernels ignore the
- * request. Synchronises the context stream. */
+ * returns. Every block of the TMA-tiled collide-stream
+ * (CACL_OPT_LB_PIPE = 3) does the same with its one tile: it gives up
+ * after 0.5 s, records it, waits once more (bounded, 0.5 s) and returns
+ * without computing. The next cacl_check_finite returns CACL_ERR_TIMEOUT;
+ * the word stays set and the state is not trusted. Other kernels ignore
+ * the request. Synchronises the context stream. */
 cacl_status cacl_inject_copy_stall(cacl_ctx* ctx, int on);
 
 /* Advance nsteps >= 0 full steps (ghost update, collide-stream, phi update,

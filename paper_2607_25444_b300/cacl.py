@@ -415,8 +415,8 @@ class Solver:
         self._check(self.L.cacl_inject_wait_timeout(self.h))
 
     def inject_copy_stall(self, on=True):
-        """Test hook: make the copy-staged collide-stream's first waits run
-        out (CACL_OPT_LB_PIPE = 1; each after 0.5 s)."""
+        """Test hook: make the copy-staged and TMA-tiled collide-stream's
+        first waits run out (CACL_OPT_LB_PIPE = 1 or 3; each after 0.5 s)."""
         self._check(self.L.cacl_inject_copy_stall(self.h, 1 if on else 0))
 
     def adjoint_timing(self):

@@ -1109,7 +1109,9 @@ lb_collide_tma(const __grid_constant__ LbTmaArgs m,
   if (tid < 32) {
     if (tid == 0) {
       mbar_init(bar, 1);
-      mbar_arrive_expect_tx(bar, L::TX_BYTES);
+      // wait_err[1]: the test request of cacl_inject_copy_stall (16 bytes
+      // more than the copies deliver, so that the wait below runs out)
+      mbar_arrive_expect_tx(bar, L::TX_BYTES + (wait_err[1] ? 16u : 0u));
     }
     __syncwarp();
     if (tid < 9) {

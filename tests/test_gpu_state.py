@@ -90,17 +90,19 @@ def test_injected_wait_timeout_is_reported():
     s.close()
 
 
-def test_copy_wait_runs_out_and_is_reported():
-    """The copy-staged collide-stream's bounded wait made to run out (each
-    block registers 16 bytes more than its first copies deliver): the step
-    ends after the wait's 0.5-s limit, cacl_check_finite reports
-    CACL_ERR_TIMEOUT, and the device stays usable: a new context with the
-    same pipeline steps bit for bit like the default pipeline."""
+@pytest.mark.parametrize("pipe", [1, 3])
+def test_copy_wait_runs_out_and_is_reported(pipe):
+    """The bounded wait of the copy-staged (pipeline 1) and TMA-tiled
+    (pipeline 3) collide-stream made to run out (each block registers 16
+    bytes more than its first copies deliver): the step ends after the
+    wait's 0.5-s limit, cacl_check_finite reports CACL_ERR_TIMEOUT, and the
+    device stays usable: a new context with the same pipeline steps bit for
+    bit like the default pipeline."""
     import time
     from paper_2607_25444_b300 import cacl
-    p, solid, phi = _case("f32")
+    p, solid, phi = _case("f32", n=(32, 16, 12))
     s = _solver(p, solid)
-    s.set_option(cacl.OPT_LB_PIPE, 1)
+    s.set_option(cacl.OPT_LB_PIPE, pipe)
     s.set_fields(phi)
     s.step(2)
     s.check_finite()
@@ -118,7 +120,7 @@ def test_copy_wait_runs_out_and_is_reported():
     s.close()
 
     a = _solver(p, solid)
-    a.set_option(cacl.OPT_LB_PIPE, 1)
+    a.set_option(cacl.OPT_LB_PIPE, pipe)
     a.set_fields(phi)
     a.step(3)
     a.check_finite()
