@@ -491,7 +491,8 @@ struct cacl_ctx {
   int* bad_flag = nullptr;  // device word for cacl_check_finite
   // [0] phase-update blocks done (the last one finalises), [1] set when a
   // bounded wait for asynchronous copies gave up, [2] test request that
-  // makes the copy-staged collide-stream's first waits run out
+  // makes the first copy waits of the staged and TMA-tiled collide-stream
+  // run out
   unsigned* ticket = nullptr;
   AdjointState* adj = nullptr;  // checkpoints, tape and adjoint fields
   int64_t device_bytes = 0;

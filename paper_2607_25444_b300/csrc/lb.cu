@@ -985,10 +985,12 @@ __device__ __forceinline__ void lb_pair_block(const typename Store::T* __restric
   }
 }
 
-// FP32 populations: at most 96 registers (five blocks of 128 per SM, no
-// spills); 16-bit populations: the compiler's own choice (96, no spills).
+// FP32 populations: at most 80 registers (six blocks of 128 per SM; 4 bytes
+// of spills): 0.625 ms per 256^3 launch against 0.647 at 96 registers (five
+// blocks, no spills), 0.707 at 128 and 0.725 at 72 (seven blocks, 120 bytes
+// of spills); 16-bit populations: the compiler's own choice (96, no spills).
 template <typename Store>
-__global__ void __launch_bounds__(LB2_PX * LB2_PY, 5)
+__global__ void __launch_bounds__(LB2_PX * LB2_PY, 6)
 lb_collide_pair32(const typename Store::T* __restrict__ fin,
                   typename Store::T* __restrict__ fout, const float* __restrict__ phi,
                   float* __restrict__ u, float* __restrict__ a,
