@@ -988,7 +988,9 @@ __device__ __forceinline__ void lb_pair_block(const typename Store::T* __restric
 // FP32 populations: at most 80 registers (six blocks of 128 per SM; 4 bytes
 // of spills): 0.625 ms per 256^3 launch against 0.647 at 96 registers (five
 // blocks, no spills), 0.707 at 128 and 0.725 at 72 (seven blocks, 120 bytes
-// of spills); 16-bit populations: the compiler's own choice (96, no spills).
+// of spills). 16-bit populations (the two-node form runs when nx is 2 mod
+// 4): six blocks as well, FP16 at 250^3 0.494 ms per launch against 0.521
+// at the compiler's own 96 registers (BF16 0.488 against 0.494).
 template <typename Store>
 __global__ void __launch_bounds__(LB2_PX * LB2_PY, 6)
 lb_collide_pair32(const typename Store::T* __restrict__ fin,
@@ -999,7 +1001,7 @@ lb_collide_pair32(const typename Store::T* __restrict__ fin,
 }
 
 template <typename Store>
-__global__ void __launch_bounds__(LB2_PX * LB2_PY)
+__global__ void __launch_bounds__(LB2_PX * LB2_PY, 6)
 lb_collide_pair16(const typename Store::T* __restrict__ fin,
                   typename Store::T* __restrict__ fout, const float* __restrict__ phi,
                   float* __restrict__ u, float* __restrict__ a,
