@@ -1503,11 +1503,13 @@ moments_init(float* __restrict__ C0, float* __restrict__ C1, float* __restrict__
 // one block per work item (the block scheduler does the distribution).
 // Registers: at most 168 for four nodes (three blocks of 128 threads per
 // SM; at 128 the case cursor and the linear indexing push the four-node
-// body into 300 bytes of spills), 96 for two (five blocks of 128), 64 for
-// one (eight blocks of 128; the single-case one-node kernel needs 56).
+// body into 300 bytes of spills), 96 for two (five blocks of 128; six
+// blocks made the 48-case sweep 1.7% slower), 85 for one (80 used, six
+// blocks of 128; at 64, eight blocks, the persistent forms spill 116 bytes
+// and the sweep ran 0.35% slower).
 template <int W, int BX>
 constexpr int lb_batch_minb() {
-  return W == 4 ? (384 + BX - 1) / BX : (W == 2 ? 640 / BX : 1024 / BX);
+  return W == 4 ? (384 + BX - 1) / BX : (W == 2 ? 640 / BX : 768 / BX);
 }
 
 template <typename Store, int W, int BX, bool PERSIST>
